@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the voxel-driven cone-beam backprojection on GB300.
+
+Workload (the paper's RabbitCT case, Sect. 3.1): a 512^3 float32 volume
+(256 mm cube, 0.5 mm voxels) reconstructed from 496 projections of
+1248 x 960 pixels over a 200-degree C-arm short scan.  Data: the seeded
+uniform [0, 1) timing stack (synthetic; the RabbitCT data set is not
+available).  One step = one full reconstruction: reset the volume,
+backproject all 496 projections, read the volume out.
+
+Metric: GUP/s = L^3 * N / t (SI giga voxel updates per second with the
+nominal count, Sect. 3.2), for FP32 projections (the headline `value`) and
+the FP16 / BF16 projection-storage forms, plus the fraction of the
+gather/FP32 roofline of the backprojection kernel.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank reconstructs its own volume (independent problems,
+weak scaling, no collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GUP/s at 512³×496 proj: FP32 vs FP16-projection form, % of roofline"
+UNIT = "GUP/s"
+
+# GB300 unit counts used for the roofline (per SM per clock):
+#   texture gathers: 4 quad-texel (tld4) results per SM per clock (one per
+#     texture unit, 4 texture units per SM);
+#   FP32 lanes: 128 per SM per clock; the kernel issues 18.5 FP32-pipe
+#     instructions per update (counted from its source: 3 FFMA geometry,
+#     2 FMUL u/v, 2 floor, 2 FADD fractions, 3 FADD + 3 FFMA interpolation,
+#     1 FMUL + 1 FFMA weight/accumulate, plus 6 FFMA per 4 voxels for the
+#     y/z terms);
+#   MUFU reciprocal: 16 per SM per clock.
+SMS = 152
+GATHER_PER_SM_CLK = 4.0
+FP32_PER_SM_CLK = 128.0
+FP32_INSTR_PER_UPDATE = 18.5
+MUFU_PER_SM_CLK = 16.0
+
+
+def roofline_peak_gups(sm_mhz: float, sms: int = SMS) -> dict:
+    f = sm_mhz * 1e6
+    bounds = {
+        "gather": sms * GATHER_PER_SM_CLK * f / 1e9,
+        "fp32_issue": sms * FP32_PER_SM_CLK / FP32_INSTR_PER_UPDATE * f / 1e9,
+        "mufu": sms * MUFU_PER_SM_CLK * f / 1e9,
+    }
+    bounds["min"] = min(bounds.values())
+    return bounds
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.err = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:  # nvidia-smi missing
+            self.err = str(e)
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        if self.err or not getattr(self, "lines", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": self.err or "no samples"}
+        sm, smax, pw, reasons = [], None, [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": "unparsable samples"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "power_w_max": max(pw),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_id_for_smi(torch, dev: int) -> str | None:
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+        dom = torch.cuda.get_device_properties(dev).pci_domain_id
+        devid = torch.cuda.get_device_properties(dev).pci_device_id
+        return f"{dom:08x}:{bus:02x}:{devid:02x}.0"
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis and "," not in vis:
+            return vis
+        return None
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(L: int, n_sample: int):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload: the
+    full L^3 volume backprojected from the first n_sample projections, with
+    OpenMP schedule(static,1) over z (the paper's Sect. 6 scheme)."""
+    import numpy as np
+
+    import oracle
+    from paper_1104_5243_gb300 import synth
+    scan, vol = synth.SCANS["full"], synth.Volume(L)
+    oracle.build()
+    A = oracle.carm_matrices(scan)[:n_sample]
+    stack = synth.uniform_stack(n_sample, scan.isy, scan.isx, seed=synth.TIMING_SEED)
+    out = np.zeros((L, L, L), dtype=np.float64)
+    t0 = time.perf_counter()
+    oracle.backproject(L, vol.R, vol.O, stack, A, vol=out)
+    dt = time.perf_counter() - t0
+    gups = L ** 3 * n_sample / dt / 1e9
+    return {"value": round(gups, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{L}^3 volume x first {n_sample} of 496 projections (1248x960), FP64, "
+                      f"{dt:.1f} s", "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.L, args.cpu_proj)
+    steps = []
+    for _ in range(args.steps):
+        c = cpu_baseline(args.L, args.ref_proj) if args.ref_proj != args.cpu_proj else cb
+        steps.append(c["value"])
+    value = statistics.median(steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"backprojection {args.L}^3 x 496 x 1248x960 (bounded sample)",
+                   "L": args.L, "n_proj": 496, "detector": [1248, 960]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                         "sample": cb["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=512)
+    ap.add_argument("--forms", default="f32,f16,bf16")
+    ap.add_argument("--cpu-proj", type=int, default=16, help="projections in the oracle sample")
+    ap.add_argument("--ref-proj", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    from paper_1104_5243_gb300 import build as native_build
+    native_build.build()
+    from paper_1104_5243_gb300 import _native as N
+    from paper_1104_5243_gb300 import api, synth
+
+    scan, vol = synth.SCANS["full"], synth.Volume(args.L)
+    A = api.carm_matrices(scan)                         # FP64 on the GPU
+    stack_host = torch.from_numpy(synth.uniform_stack(scan.n, scan.isy, scan.isx)).pin_memory()
+    stack = stack_host.cuda()
+    updates = args.L ** 3 * scan.n
+    out = torch.empty((args.L,) * 3, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    smi_id = gpu_id_for_smi(torch, local_rank)
+    forms = {}
+    kernel = {}
+    clocks = None
+    for form in args.forms.split(","):
+        bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=form)
+
+        def step():
+            bp.reset()
+            bp.add_projections(stack, A)
+            bp.finalize(out)
+
+        for _ in range(args.warmup):
+            step()
+        bp.set_option(N.BP_OPT_TIMING, 1)
+        bp.kernel_stats()
+        barrier()
+        with ClockSampler(smi_id) as cs:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(args.steps):
+                step()
+            t1.record(stream)
+            torch.cuda.synchronize()
+        ms = max_over_ranks(t0.elapsed_time(t1))
+        launches, kms = bp.kernel_stats()
+        bp.set_option(N.BP_OPT_TIMING, 0)
+        gups = updates * args.steps * world / (ms / 1e3) / 1e9
+        forms[form] = {"value": round(gups, 2), "ms_per_step": round(ms / args.steps, 3)}
+        kernel[form] = {"launches": launches, "kernel_ms": kms,
+                        "kernel_gups": updates * args.steps / (kms / 1e3) / 1e9 if kms > 0 else None}
+        if form == "f32":
+            clocks = cs.summary()
+        bp.close()
+
+    # End to end through the public API: pinned host projections in, volume
+    # out to pinned host memory, every step.
+    e2e = None
+    if not args.no_e2e:
+        vol_host = torch.empty((args.L,) * 3, dtype=torch.float32).pin_memory()
+        bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype="f32")
+
+        def step_e2e():
+            bp.reset()
+            bp.add_projections(stack_host, A)
+            bp.finalize(vol_host)
+
+        for _ in range(args.warmup):
+            step_e2e()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_e2e()
+        torch.cuda.synchronize()
+        wall = max_over_ranks(time.perf_counter() - t0)
+        bp.close()
+        e2e = {"value": round(updates * args.steps * world / wall / 1e9, 2), "unit": UNIT,
+               "h2d_bytes_per_step": int(stack_host.numel() * 4),
+               "d2h_bytes_per_step": int(vol_host.numel() * 4)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    f32 = forms.get("f32") or next(iter(forms.values()))
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = roofline_peak_gups(sm_mhz)
+    k = kernel.get("f32") or next(iter(kernel.values()))
+    achieved = k["kernel_gups"]
+    roofline = {
+        "bound": "alu", "unit": UNIT, "kernel": "bp_fwd_kernel (FP32 projections)",
+        "achieved": round(achieved, 2) if achieved else None,
+        "peak": round(peak["min"], 1),
+        "frac": round(achieved / peak["min"], 4) if achieved else None,
+        "peak_at_sm_mhz": sm_mhz,
+        "bounds_gups": {kk: round(v, 1) for kk, v in peak.items()},
+        "avg_launch_ms": round(k["kernel_ms"] / max(k["launches"], 1), 4),
+        "launches": k["launches"],
+        "traffic": None,
+    }
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.L, args.cpu_proj)
+    line = {
+        "metric": METRIC, "value": f32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": f32["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"FDK backprojection {args.L}^3 x {scan.n} x {scan.isx}x{scan.isy}, "
+                               "uniform [0,1) stack seed 20110426, 200-degree C-arm",
+                   "L": args.L, "n_proj": scan.n, "detector": [scan.isx, scan.isy],
+                   "l2": "inputs larger than L2 (2.38 GB projections + 0.54 GB volume per step)",
+                   "step": "reset + bp_add_projections(496, device-resident) + finalize"},
+        "forms": {kk: {**v, "frac_of_roofline": round(v["value"] / world / peak["min"], 4)}
+                  for kk, v in forms.items()},
+        "kernel_events": {kk: {"launches": v["launches"], "kernel_ms": round(v["kernel_ms"], 3)}
+                          for kk, v in kernel.items()},
+        "roofline": roofline,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": sum(v["launches"] for v in kernel.values()),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * bp1104.h -- C ABI of the GB300 voxel-driven cone-beam backprojection
+ * library (libbp1104.so).
+ *
+ * The method is the Feldkamp backprojection step studied by Treibig, Hager,
+ * Hofmann, Hornegger and Wellein, "Pushing the limits for medical image
+ * reconstruction on recent standard multicore processors" (Sect. 3.1,
+ * Listing 1): for every voxel x of an L^3 volume and every filtered
+ * projection image I_i with 3x4 projection matrix A_i,
+ *
+ *     (uw, vw, w) = A_i (x, 1),   u = uw / w,   v = vw / w
+ *     VOL[x] += bilinear(I_i, u, v) / w^2
+ *
+ * where pixel (j, k) of an ISX x ISY image sits at (u, v) = (j, k) and pixels
+ * outside the detector read as zero (the zero-padded image buffers of
+ * Sect. 3.3).  The integer part of u and v is floor().
+ *
+ * Conventions for every entry point:
+ *   - Volumes are L^3 float32, x fastest: index z*L*L + y*L + x.  Voxel
+ *     (x, y, z) sits at world position O + R (x, y, z) in mm (Sect. 3.1: the
+ *     volume is a 256 mm cube, R = 256 / L).
+ *   - Projection stacks are n x ISY x ISX float32, row-major (I[k*ISX + j]).
+ *   - Matrices are n x 3 x 4 float64, ROW-major (A[r*4 + c]; rows give uw,
+ *     vw, w).  The paper's listing indexes the same matrix column-major.
+ *   - "on_device" flags say whether a pointer is device memory (1) or host
+ *     memory (0).  Host buffers should be page-locked for asynchronous copies.
+ *   - The caller owns every buffer it passes.  Calls are asynchronous on the
+ *     context's CUDA stream unless stated otherwise: buffers must stay valid
+ *     and unmodified until the next bp_finalize / bp_get_state or a stream
+ *     synchronisation.
+ *   - Errors are status codes; nothing aborts or throws.  bp_last_error(ctx)
+ *     returns the message of the last failure on that context
+ *     (bp_last_error(NULL): the calling thread's last failure in a function
+ *     without a context).
+ *   - All arithmetic on the GPU is float32 except where noted; float64 is used
+ *     on the GPU only to build and invert projection matrices.
+ */
+#ifndef BP1104_H
+#define BP1104_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bp_ctx bp_ctx;
+
+typedef enum {
+    BP_OK = 0,        /* success */
+    BP_EINVAL = 1,    /* invalid argument (size, pointer, geometry) */
+    BP_ENOMEM = 2,    /* device or pinned allocation failed */
+    BP_ECUDA = 3,     /* a CUDA runtime call failed; see bp_last_error */
+    BP_ESTATE = 4,    /* call not allowed in the context's current state */
+    BP_ETIMEOUT = 5   /* a bounded device-side wait gave up */
+} bp_status;
+
+/* Storage type of the projections inside the library (Sect. 3.1 uses single
+ * precision; FP16 / BF16 halve the bytes gathered per update).  Coordinates,
+ * the 1/w^2 weight and the accumulation are float32 for every type. */
+typedef enum { BP_F32 = 0, BP_F16 = 1, BP_BF16 = 2 } bp_dtype;
+
+/* Options for bp_set_option. */
+typedef enum {
+    /* 1: reciprocal 1/w by the IEEE round-to-nearest division; 0 (default):
+     * the hardware approximate reciprocal (about 1 ulp).  Sect. 7.2 compares
+     * the same two choices (divps against rcpps). */
+    BP_OPT_IEEE_RCP = 1,
+    /* Projections per volume pass, 1..64 (default 64).  The volume is read
+     * and written once per pass (the image blocking of Sect. 6.2). */
+    BP_OPT_BATCH = 2,
+    /* 1: record a CUDA event pair around every backprojection kernel launch
+     * on the context's stream, for bp_kernel_stats; 0 (default): off. */
+    BP_OPT_TIMING = 3,
+    /* Warp layout of the backprojection kernel: lanes along x (8, 16 or 32;
+     * the rest along z).  Default 8.  Changes speed, not results beyond
+     * float32 summation order. */
+    BP_OPT_LANES_X = 4
+} bp_option;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a backprojection context for an L^3 volume of voxel size R (mm)
+ * whose voxel (0,0,0) centre is at O[0..2] (mm), and ISX x ISY projections
+ * stored as proj_dtype.  cuda_stream is the cudaStream_t every later call on
+ * this context is ordered on (NULL: the legacy default stream); it is fixed
+ * for the context's lifetime.  The context allocates the
+ * device volume (zeroed) and the projection staging on the current device.
+ * Sect. 3.1 (problem statement: L, MM, offsets, ISX x ISY images).
+ * Returns BP_EINVAL for L < 1, R <= 0, ISX or ISY outside [1, 32768], or
+ * a NULL out; BP_ENOMEM when the device allocations fail. */
+bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
+                    int isx, int isy, bp_dtype proj_dtype, void *cuda_stream);
+
+/* Release everything the context owns (synchronises its stream first).
+ * NULL is accepted and ignored. */
+bp_status bp_destroy(bp_ctx *ctx);
+
+/* Set a bp_option (see above).  BP_EINVAL for an unknown option or value. */
+bp_status bp_set_option(bp_ctx *ctx, int option, long long value);
+
+/* Zero the volume and the projection counter (asynchronous). */
+bp_status bp_reset(bp_ctx *ctx);
+
+/* Accumulate n projections into the volume (Sect. 3.1, Listing 1; images
+ * arrive one by one or in batches, Sect. 6):
+ *   images: n x ISY x ISX float32, host (images_on_device = 0) or device;
+ *   A:      n x 3 x 4 float64 row-major, HOST memory, read before return.
+ * VOL += sum_i bilinear(I_i, A_i x) / w^2 over the n images.  Every voxel of
+ * the volume must lie in front of every source (w > 0 at the 8 corners of
+ * the volume box), else BP_EINVAL.  n = 0 is a no-op.  Host images are
+ * copied while earlier batches compute; the call returns when the last copy
+ * has been queued. */
+bp_status bp_add_projections(bp_ctx *ctx, const float *images, int images_on_device,
+                             const double *A, int n);
+
+/* Synchronise the stream and copy the volume (L^3 float32) to vol_out (host
+ * or device).  The context stays usable; further bp_add_projections keep
+ * accumulating onto the same volume until bp_reset. */
+bp_status bp_finalize(bp_ctx *ctx, float *vol_out, int on_device);
+
+/* Checkpoint: copy the partial volume and the number of projections added so
+ * far (synchronous).  vol_out may be NULL to read only the counter. */
+bp_status bp_get_state(bp_ctx *ctx, float *vol_out, int on_device, long long *n_added);
+
+/* Resume: replace the volume by vol_in (L^3 float32, host or device) and set
+ * the projection counter.  Continuing from a saved state gives the same
+ * volume, bit for bit, as one uninterrupted run with the same batches. */
+bp_status bp_set_state(bp_ctx *ctx, const float *vol_in, int on_device, long long n_added);
+
+/* Adjoint (transpose) of the backprojection: for every voxel value f(x) and
+ * projection i, spread f(x) / w^2 onto the four pixels around (u, v) with the
+ * bilinear weights (1-fu)(1-fv), fu(1-fv), (1-fu)fv, fu fv; pixels outside
+ * the detector are dropped.  This is the transpose of the sum in Listing 1
+ * (Sect. 3.1): <B p, f> = <p, B^T f>.
+ *   vol:        L^3 float32 (host or device per vol_on_device);
+ *   A:          n x 3 x 4 float64 row-major, HOST memory;
+ *   images_out: n x ISY x ISX float32 (host or device per out_on_device),
+ *               overwritten (the callee zeroes it first).
+ * Uses float32 atomics, so the summation order (and the last bits) can vary
+ * between runs.  Leaves the context's volume untouched. */
+bp_status bp_adjoint(bp_ctx *ctx, const float *vol, int vol_on_device,
+                     const double *A, int n, float *images_out, int out_on_device);
+
+/* Device time of the backprojection kernel launches recorded while
+ * BP_OPT_TIMING was on (measurement support, in the spirit of the paper's
+ * hardware-counter timelines, Sect. 7): synchronises the stream, returns the
+ * number of launches and their summed CUDA-event time in ms, and clears the
+ * record.  Either output pointer may be NULL. */
+bp_status bp_kernel_stats(bp_ctx *ctx, long long *launches, double *total_ms);
+
+/* Message of the last failure on ctx (or, for ctx == NULL, of the calling
+ * thread's last failing context-free call).  Never NULL. */
+const char *bp_last_error(const bp_ctx *ctx);
+
+/* ------------------------------------------------------ context-free calls
+ * All pointers below are DEVICE pointers unless stated; work is queued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream). */
+
+/* Projection matrices of a circular C-arm scan about z, built in float64 on
+ * the GPU: source at sid (cos b, sin b, 0), detector at distance sdd from the
+ * source with u axis (-sin b, cos b, 0), v axis (0, 0, 1), square pixels of
+ * `pitch` mm and principal point (cu, cv); scaled so that w = depth / sid.
+ * beta: n angles in radians (HOST); A_out: n x 12 float64 (device). */
+bp_status bp_carm_matrices(int n, const double *beta, double sid, double sdd, double pitch,
+                           double cu, double cv, double *A_out, void *stream);
+
+/* Analytic line integrals of an additive ellipsoid phantom (test data for
+ * the FDK pipeline, Sect. 1.1): out[i][k][j] = sum_e rho_e * chord length of
+ * the ray from the source of A_i through pixel (j, k).  A: n x 12 float64
+ * (device; sources and ray directions are found by inverting A in float64);
+ * ell: count x 16 float64 (device; centre 3, semi-axes 3, row-major rotation
+ * 9 whose columns are the axes, density 1); out: n x isy x isx float32. */
+bp_status bp_ellipsoid_project(int n, const double *A, int isx, int isy, int count,
+                               const double *ell, float *out, void *stream);
+
+/* Phantom density at every voxel centre of an L^3 grid (R, O as above):
+ * vol[z][y][x] = sum of rho_e over ellipsoids containing the centre. */
+bp_status bp_ellipsoid_voxelize(int L, double R, const double O[3], int count,
+                                const double *ell, float *vol, void *stream);
+
+/* FDK pre-weighting (Sect. 1.1, 2-D pre-processing): out = in * scale *
+ * sdd / sqrt(sdd^2 + ut^2 + vt^2) * parker(b_i, atan(ut / sdd)) with
+ * ut = (j - cu) pitch, vt = (k - cv) pitch, b_i = beta[i] - beta[0] and the
+ * Parker short-scan weight for a scan of beta[n-1] - beta[0] = pi + 2 delta
+ * (parker = 0 drops that factor).  beta: HOST, n values; in/out: n x isy x
+ * isx float32 device (in == out allowed). */
+bp_status bp_fdk_preweight(int n, int isx, int isy, double pitch, double sdd, double cu,
+                           double cv, const double *beta, int parker, double scale,
+                           const float *in, float *out, void *stream);
+
+/* Ramp filter: row-wise linear (zero-padded) convolution with the Ram-Lak
+ * kernel h(0) = 1/(4 tau^2), h(odd m) = -1/(m^2 pi^2 tau^2), h(even) = 0:
+ * out[r][j] = tau * sum_j' h(j - j') in[r][j'], rows rows of isx floats.
+ * in and out must not overlap. */
+bp_status bp_ramp_filter(long long rows, int isx, double tau, const float *in, float *out,
+                         void *stream);
+
+/* Short per-row filter (the learned replacement of the ramp, T <= 128 taps):
+ * out[r][j] = sum_t h[t] in[r][j + t - T/2], zero outside the row.
+ * h: T float32 (device).  in and out must not overlap. */
+bp_status bp_row_filter_fwd(long long rows, int isx, int T, const float *h, const float *in,
+                            float *out, void *stream);
+
+/* Gradients of bp_row_filter_fwd for dL/dout = g:
+ *   gin[r][s] = sum_t h[t] g[r][s - t + T/2]           (may be NULL to skip)
+ *   gh[t]     = sum_{r,j} g[r][j] in[r][j + t - T/2]   (may be NULL to skip)
+ * gh is reduced deterministically in two passes through a scratch buffer the
+ * call allocates (stream-ordered) and frees. */
+bp_status bp_row_filter_bwd(long long rows, int isx, int T, const float *h, const float *in,
+                            const float *g, float *gin, float *gh, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BP1104_H */

@@ -1,0 +1,518 @@
+// C ABI of the backprojection context (include/bp1104.h): argument checks,
+// device allocations, the projection staging pipeline and kernel launches.
+//
+// Pipeline of bp_add_projections (images arrive one by one or in batches,
+// Sect. 6): batches of up to kMaxBatch images alternate between two sets of
+// texture-backed CUDA arrays.  A copy stream fills one set (host or device
+// source; FP16/BF16 conversion included) while the compute stream
+// backprojects the other; events order the two streams, so the compute
+// stream never reads a set before its copy finished and the copy stream
+// never overwrites a set the compute stream still reads.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bp_internal.cuh"
+
+namespace bp {
+const char *thread_error();
+}
+
+using namespace bp;
+
+struct bp_ctx {
+    int L = 0;
+    double R = 0, O[3] = {0, 0, 0};
+    int isx = 0, isy = 0;
+    bp_dtype dtype = BP_F32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    float *vol = nullptr;
+    bool vol_zero = true;         // volume known to be all zeros
+    long long n_added = 0;
+    int batch = kMaxBatch;
+    bool ieee_rcp = false;
+    int lanes_x = 8;              // warp layout of the kernel: lanes along x
+    cudaArray_t arr[2][kMaxBatch] = {};
+    cudaTextureObject_t tex[2][kMaxBatch] = {};
+    cudaSurfaceObject_t surf[2][kMaxBatch] = {};
+    float *staging[2] = {nullptr, nullptr};   // host-input staging for FP16/BF16
+    cudaEvent_t inputs_ready = nullptr;
+    cudaEvent_t copy_done[2] = {nullptr, nullptr};
+    cudaEvent_t kern_done[2] = {nullptr, nullptr};
+    int next_set = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;   // start/stop pairs, reused
+    size_t ev_used = 0;
+    char err[1024] = "no error";
+};
+
+static bp_status fail(bp_ctx *c, bp_status st, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        snprintf(c->err, sizeof c->err, "%s", buf);
+    else
+        set_thread_error("%s", buf);
+    return st;
+}
+
+#define CTX_CK(c, call)                                                              \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? BP_ENOMEM : BP_ECUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                    \
+    } while (0)
+
+static void release(bp_ctx *c)
+{
+    cudaStreamSynchronize(c->stream);
+    if (c->copy_stream)
+        cudaStreamSynchronize(c->copy_stream);
+    for (int s = 0; s < 2; ++s) {
+        for (int j = 0; j < kMaxBatch; ++j) {
+            if (c->tex[s][j])
+                cudaDestroyTextureObject(c->tex[s][j]);
+            if (c->surf[s][j])
+                cudaDestroySurfaceObject(c->surf[s][j]);
+            if (c->arr[s][j])
+                cudaFreeArray(c->arr[s][j]);
+        }
+        if (c->staging[s])
+            cudaFree(c->staging[s]);
+        if (c->copy_done[s])
+            cudaEventDestroy(c->copy_done[s]);
+        if (c->kern_done[s])
+            cudaEventDestroy(c->kern_done[s]);
+    }
+    if (c->inputs_ready)
+        cudaEventDestroy(c->inputs_ready);
+    for (cudaEvent_t e : c->ev)
+        cudaEventDestroy(e);
+    if (c->vol)
+        cudaFree(c->vol);
+    if (c->copy_stream)
+        cudaStreamDestroy(c->copy_stream);
+}
+
+static bp_status alloc_slot(bp_ctx *c, int s, int j)
+{
+    cudaChannelFormatDesc fmt;
+    if (c->dtype == BP_F32)
+        fmt = cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);
+    else if (c->dtype == BP_F16)
+        fmt = cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindFloat);
+    else
+        fmt = cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
+    const unsigned flags = c->dtype == BP_F32 ? cudaArrayDefault : cudaArraySurfaceLoadStore;
+    CTX_CK(c, cudaMallocArray(&c->arr[s][j], &fmt, c->isx, c->isy, flags));
+    cudaResourceDesc res;
+    memset(&res, 0, sizeof res);
+    res.resType = cudaResourceTypeArray;
+    res.res.array.array = c->arr[s][j];
+    cudaTextureDesc td;
+    memset(&td, 0, sizeof td);
+    td.addressMode[0] = cudaAddressModeBorder;   // zero outside the detector
+    td.addressMode[1] = cudaAddressModeBorder;
+    td.filterMode = cudaFilterModePoint;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    CTX_CK(c, cudaCreateTextureObject(&c->tex[s][j], &res, &td, nullptr));
+    if (c->dtype != BP_F32)
+        CTX_CK(c, cudaCreateSurfaceObject(&c->surf[s][j], &res));
+    return BP_OK;
+}
+
+extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3], int isx, int isy,
+                               bp_dtype proj_dtype, void *cuda_stream)
+{
+    if (out == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_create: out is NULL");
+    *out = nullptr;
+    if (L < 1 || L > 4096 || !(R > 0) || !std::isfinite(R) || O == nullptr ||
+        !std::isfinite(O[0]) || !std::isfinite(O[1]) || !std::isfinite(O[2]))
+        return fail(nullptr, BP_EINVAL, "bp_create: invalid volume (1 <= L <= 4096, R > 0, finite O)");
+    if (isx < 1 || isy < 1 || isx > 32768 || isy > 32768)
+        return fail(nullptr, BP_EINVAL, "bp_create: detector size must be in [1, 32768]");
+    if (proj_dtype != BP_F32 && proj_dtype != BP_F16 && proj_dtype != BP_BF16)
+        return fail(nullptr, BP_EINVAL, "bp_create: unknown projection dtype %d", (int)proj_dtype);
+    bp_ctx *c = new (std::nothrow) bp_ctx;
+    if (c == nullptr)
+        return fail(nullptr, BP_ENOMEM, "bp_create: out of host memory");
+    c->L = L;
+    c->R = R;
+    c->O[0] = O[0];
+    c->O[1] = O[1];
+    c->O[2] = O[2];
+    c->isx = isx;
+    c->isy = isy;
+    c->dtype = proj_dtype;
+    bp_status st = BP_OK;
+    auto check = [&](cudaError_t e, const char *what) {
+        if (st == BP_OK && e != cudaSuccess)
+            st = fail(nullptr, e == cudaErrorMemoryAllocation ? BP_ENOMEM : BP_ECUDA, "bp_create: %s: %s",
+                      what, cudaGetErrorString(e));
+    };
+    check(cudaGetDevice(&c->device), "cudaGetDevice");
+    c->stream = (cudaStream_t)cuda_stream;   // NULL: the legacy default stream
+    check(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate(copy)");
+    check(cudaEventCreateWithFlags(&c->inputs_ready, cudaEventDisableTiming), "cudaEventCreate");
+    for (int s = 0; s < 2; ++s) {
+        check(cudaEventCreateWithFlags(&c->copy_done[s], cudaEventDisableTiming), "cudaEventCreate");
+        check(cudaEventCreateWithFlags(&c->kern_done[s], cudaEventDisableTiming), "cudaEventCreate");
+    }
+    const size_t nvox = (size_t)L * L * L;
+    check(cudaMalloc((void **)&c->vol, nvox * sizeof(float)), "cudaMalloc(volume)");
+    if (st == BP_OK)
+        check(cudaMemsetAsync(c->vol, 0, nvox * sizeof(float), c->stream), "cudaMemsetAsync");
+    for (int s = 0; s < 2 && st == BP_OK; ++s)
+        for (int j = 0; j < kMaxBatch && st == BP_OK; ++j) {
+            bp_status r = alloc_slot(c, s, j);
+            if (r != BP_OK)
+                st = fail(nullptr, r, "bp_create: %s", c->err);
+        }
+    if (st == BP_OK)
+        check(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (st != BP_OK) {
+        release(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return BP_OK;
+}
+
+extern "C" bp_status bp_destroy(bp_ctx *c)
+{
+    if (c == nullptr)
+        return BP_OK;
+    release(c);
+    delete c;
+    return BP_OK;
+}
+
+extern "C" const char *bp_last_error(const bp_ctx *c)
+{
+    return c ? c->err : thread_error();
+}
+
+extern "C" bp_status bp_set_option(bp_ctx *c, int option, long long value)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_set_option: NULL context");
+    switch (option) {
+    case BP_OPT_IEEE_RCP:
+        if (value != 0 && value != 1)
+            return fail(c, BP_EINVAL, "bp_set_option: IEEE_RCP takes 0 or 1");
+        c->ieee_rcp = value != 0;
+        return BP_OK;
+    case BP_OPT_BATCH:
+        if (value < 1 || value > kMaxBatch)
+            return fail(c, BP_EINVAL, "bp_set_option: BATCH must be in [1, %d]", kMaxBatch);
+        c->batch = (int)value;
+        return BP_OK;
+    case BP_OPT_LANES_X:
+        if (value != 8 && value != 16 && value != 32)
+            return fail(c, BP_EINVAL, "bp_set_option: LANES_X takes 8, 16 or 32");
+        c->lanes_x = (int)value;
+        return BP_OK;
+    case BP_OPT_TIMING:
+        if (value != 0 && value != 1)
+            return fail(c, BP_EINVAL, "bp_set_option: TIMING takes 0 or 1");
+        c->timing = value != 0;
+        return BP_OK;
+    default:
+        return fail(c, BP_EINVAL, "bp_set_option: unknown option %d", option);
+    }
+}
+
+extern "C" bp_status bp_reset(bp_ctx *c)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_reset: NULL context");
+    CTX_CK(c, cudaSetDevice(c->device));
+    CTX_CK(c, cudaMemsetAsync(c->vol, 0, sizeof(float) * (size_t)c->L * c->L * c->L, c->stream));
+    c->vol_zero = true;
+    c->n_added = 0;
+    return BP_OK;
+}
+
+// Host-side checks of the matrices: finite entries and w > 0 at the eight
+// corners of the volume box (w is affine in x, so then w > 0 everywhere).
+static bp_status check_matrices(bp_ctx *c, const char *who, const double *A, int n)
+{
+    for (int i = 0; i < n; ++i) {
+        const double *a = A + 12 * (size_t)i;
+        for (int q = 0; q < 12; ++q)
+            if (!std::isfinite(a[q]))
+                return fail(c, BP_EINVAL, "%s: matrix %d has a non-finite entry", who, i);
+        for (int corner = 0; corner < 8; ++corner) {
+            const double X = c->O[0] + c->R * ((corner & 1) ? c->L - 1 : 0);
+            const double Y = c->O[1] + c->R * ((corner & 2) ? c->L - 1 : 0);
+            const double Z = c->O[2] + c->R * ((corner & 4) ? c->L - 1 : 0);
+            const double w = a[8] * X + a[9] * Y + a[10] * Z + a[11];
+            if (!(w > 0))
+                return fail(c, BP_EINVAL,
+                            "%s: matrix %d puts part of the volume behind the source (w <= 0)", who, i);
+        }
+    }
+    return BP_OK;
+}
+
+static inline float4 row4(const double *a, int r, double add_w)
+{
+    // row r of A, plus add_w times the w row (folds the centring and gather
+    // offsets in float64 before rounding to float32)
+    return make_float4((float)(a[4 * r] + add_w * a[8]), (float)(a[4 * r + 1] + add_w * a[9]),
+                       (float)(a[4 * r + 2] + add_w * a[10]), (float)(a[4 * r + 3] + add_w * a[11]));
+}
+
+// Integer centring offsets (ku, kv): the pixel the centre of the volume
+// projects to, rounded.  Over the volume |u - ku| then stays within the
+// volume's footprint half-width, far below |u|.
+static inline void centre_offsets(const bp_ctx *c, const double *a, double *ku, double *kv)
+{
+    const double h = 0.5 * (c->L - 1) * c->R;
+    const double X = c->O[0] + h, Y = c->O[1] + h, Z = c->O[2] + h;
+    const double w = a[8] * X + a[9] * Y + a[10] * Z + a[11];
+    const double u = (a[0] * X + a[1] * Y + a[2] * Z + a[3]) / w;
+    const double v = (a[4] * X + a[5] * Y + a[6] * Z + a[7]) / w;
+    *ku = std::fmin(std::fmax(std::nearbyint(u), -1048576.0), 1048576.0);
+    *kv = std::fmin(std::fmax(std::nearbyint(v), -1048576.0), 1048576.0);
+}
+
+static VolGeom vol_geom(const bp_ctx *c)
+{
+    VolGeom g;
+    g.L = c->L;
+    g.R = (float)c->R;
+    g.Ox = (float)c->O[0];
+    g.Oy = (float)c->O[1];
+    g.Oz = (float)c->O[2];
+    return g;
+}
+
+extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int images_on_device,
+                                        const double *A, int n)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_add_projections: NULL context");
+    if (n < 0)
+        return fail(c, BP_EINVAL, "bp_add_projections: n < 0");
+    if (n == 0)
+        return BP_OK;
+    if (images == nullptr || A == nullptr)
+        return fail(c, BP_EINVAL, "bp_add_projections: NULL images or matrices");
+    bp_status st = check_matrices(c, "bp_add_projections", A, n);
+    if (st != BP_OK)
+        return st;
+    CTX_CK(c, cudaSetDevice(c->device));
+    const size_t img_elems = (size_t)c->isx * c->isy;
+    const size_t row_bytes = sizeof(float) * c->isx;
+    const cudaMemcpyKind kind = images_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // Work queued on the caller's stream before this call (e.g. the producer
+    // of device images) must finish before the copy stream reads.
+    CTX_CK(c, cudaEventRecord(c->inputs_ready, c->stream));
+    CTX_CK(c, cudaStreamWaitEvent(c->copy_stream, c->inputs_ready, 0));
+    const VolGeom g = vol_geom(c);
+    for (int c0 = 0; c0 < n; c0 += c->batch) {
+        const int m = n - c0 < c->batch ? n - c0 : c->batch;
+        const int s = c->next_set;
+        c->next_set ^= 1;
+        CTX_CK(c, cudaStreamWaitEvent(c->copy_stream, c->kern_done[s], 0));
+        const float *src0 = images + (size_t)c0 * img_elems;
+        if (c->dtype == BP_F32) {
+            for (int j = 0; j < m; ++j)
+                CTX_CK(c, cudaMemcpy2DToArrayAsync(c->arr[s][j], 0, 0, src0 + (size_t)j * img_elems, row_bytes,
+                                                   row_bytes, c->isy, kind, c->copy_stream));
+        } else {
+            const float *src = src0;
+            if (!images_on_device) {
+                if (c->staging[s] == nullptr)
+                    CTX_CK(c, cudaMalloc((void **)&c->staging[s], sizeof(float) * img_elems * kMaxBatch));
+                CTX_CK(c, cudaMemcpyAsync(c->staging[s], src0, sizeof(float) * img_elems * m,
+                                          cudaMemcpyHostToDevice, c->copy_stream));
+                src = c->staging[s];
+            }
+            ConvBatch cb;
+            cb.n = m;
+            for (int j = 0; j < m; ++j) {
+                cb.src[j] = src + (size_t)j * img_elems;
+                cb.surf[j] = c->surf[s][j];
+            }
+            CTX_CK(c, launch_convert(cb, c->isx, c->isy, c->dtype == BP_BF16, c->copy_stream));
+        }
+        CTX_CK(c, cudaEventRecord(c->copy_done[s], c->copy_stream));
+        CTX_CK(c, cudaStreamWaitEvent(c->stream, c->copy_done[s], 0));
+        FwdBatch b;
+        b.n = m;
+        for (int j = 0; j < m; ++j) {
+            const double *a = A + 12 * (size_t)(c0 + j);
+            // u' = u - ku + 1 = (uw - (ku - 1) w) / w; gather at floor(u') + ku
+            double ku, kv;
+            centre_offsets(c, a, &ku, &kv);
+            b.m[j][0] = row4(a, 0, 1.0 - ku);
+            b.m[j][1] = row4(a, 1, 1.0 - kv);
+            b.m[j][2] = row4(a, 2, 0.0);
+            b.k[j] = make_float2((float)ku, (float)kv);
+            b.tex[j] = c->tex[s][j];
+        }
+        cudaEvent_t ev_stop = nullptr;
+        if (c->timing) {
+            while (c->ev.size() < c->ev_used + 2) {
+                cudaEvent_t e;
+                CTX_CK(c, cudaEventCreate(&e));
+                c->ev.push_back(e);
+            }
+            CTX_CK(c, cudaEventRecord(c->ev[c->ev_used], c->stream));
+            ev_stop = c->ev[c->ev_used + 1];
+            c->ev_used += 2;
+        }
+        CTX_CK(c, launch_bp_fwd(b, c->vol, g, c->dtype == BP_BF16 ? kTexBF16 : kTexFloat, !c->vol_zero,
+                                c->ieee_rcp, c->lanes_x, c->stream));
+        if (ev_stop)
+            CTX_CK(c, cudaEventRecord(ev_stop, c->stream));
+        c->vol_zero = false;
+        CTX_CK(c, cudaEventRecord(c->kern_done[s], c->stream));
+    }
+    c->n_added += n;
+    return BP_OK;
+}
+
+extern "C" bp_status bp_kernel_stats(bp_ctx *c, long long *launches, double *total_ms)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_kernel_stats: NULL context");
+    CTX_CK(c, cudaSetDevice(c->device));
+    CTX_CK(c, cudaStreamSynchronize(c->stream));
+    double ms = 0.0;
+    for (size_t q = 0; q + 1 < c->ev_used; q += 2) {
+        float t = 0.f;
+        CTX_CK(c, cudaEventElapsedTime(&t, c->ev[q], c->ev[q + 1]));
+        ms += t;
+    }
+    if (launches)
+        *launches = (long long)(c->ev_used / 2);
+    if (total_ms)
+        *total_ms = ms;
+    c->ev_used = 0;
+    return BP_OK;
+}
+
+extern "C" bp_status bp_finalize(bp_ctx *c, float *vol_out, int on_device)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_finalize: NULL context");
+    if (vol_out == nullptr)
+        return fail(c, BP_EINVAL, "bp_finalize: NULL output");
+    CTX_CK(c, cudaSetDevice(c->device));
+    const size_t bytes = sizeof(float) * (size_t)c->L * c->L * c->L;
+    CTX_CK(c, cudaMemcpyAsync(vol_out, c->vol, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              c->stream));
+    CTX_CK(c, cudaStreamSynchronize(c->stream));
+    return BP_OK;
+}
+
+extern "C" bp_status bp_get_state(bp_ctx *c, float *vol_out, int on_device, long long *n_added)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_get_state: NULL context");
+    if (vol_out != nullptr) {
+        bp_status st = bp_finalize(c, vol_out, on_device);
+        if (st != BP_OK)
+            return st;
+    }
+    if (n_added)
+        *n_added = c->n_added;
+    return BP_OK;
+}
+
+extern "C" bp_status bp_set_state(bp_ctx *c, const float *vol_in, int on_device, long long n_added)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_set_state: NULL context");
+    if (vol_in == nullptr || n_added < 0)
+        return fail(c, BP_EINVAL, "bp_set_state: NULL volume or negative counter");
+    CTX_CK(c, cudaSetDevice(c->device));
+    const size_t bytes = sizeof(float) * (size_t)c->L * c->L * c->L;
+    CTX_CK(c, cudaMemcpyAsync(c->vol, vol_in, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+    CTX_CK(c, cudaStreamSynchronize(c->stream));
+    c->vol_zero = false;
+    c->n_added = n_added;
+    return BP_OK;
+}
+
+extern "C" bp_status bp_adjoint(bp_ctx *c, const float *vol, int vol_on_device, const double *A, int n,
+                                float *images_out, int out_on_device)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_adjoint: NULL context");
+    if (n < 0)
+        return fail(c, BP_EINVAL, "bp_adjoint: n < 0");
+    if (n == 0)
+        return BP_OK;
+    if (vol == nullptr || A == nullptr || images_out == nullptr)
+        return fail(c, BP_EINVAL, "bp_adjoint: NULL volume, matrices or output");
+    bp_status st = check_matrices(c, "bp_adjoint", A, n);
+    if (st != BP_OK)
+        return st;
+    CTX_CK(c, cudaSetDevice(c->device));
+    const size_t nvox = (size_t)c->L * c->L * c->L;
+    const size_t img_elems = (size_t)c->isx * c->isy;
+    const float *dvol = vol;
+    float *dvol_tmp = nullptr, *dout = images_out;
+    cudaError_t e = cudaSuccess;
+    if (!vol_on_device) {
+        e = cudaMallocAsync((void **)&dvol_tmp, sizeof(float) * nvox, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dvol_tmp, vol, sizeof(float) * nvox, cudaMemcpyHostToDevice, c->stream);
+        dvol = dvol_tmp;
+    }
+    float *dout_tmp = nullptr;
+    if (e == cudaSuccess && !out_on_device) {
+        e = cudaMallocAsync((void **)&dout_tmp, sizeof(float) * img_elems * n, c->stream);
+        dout = dout_tmp;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(dout, 0, sizeof(float) * img_elems * n, c->stream);
+    const VolGeom g = vol_geom(c);
+    for (int c0 = 0; e == cudaSuccess && c0 < n; c0 += kMaxBatch) {
+        const int m = n - c0 < kMaxBatch ? n - c0 : kMaxBatch;
+        AdjBatch b;
+        b.n = m;
+        for (int j = 0; j < m; ++j) {
+            const double *a = A + 12 * (size_t)(c0 + j);
+            double ku, kv;
+            centre_offsets(c, a, &ku, &kv);
+            b.m[j][0] = row4(a, 0, -ku);
+            b.m[j][1] = row4(a, 1, -kv);
+            b.m[j][2] = row4(a, 2, 0.0);
+            b.k[j] = make_int2((int)ku, (int)kv);
+            b.out_off[j] = (long long)(c0 + j) * (long long)img_elems;
+        }
+        e = launch_bp_adjoint(b, dvol, g, dout, c->isx, c->isy, c->ieee_rcp, c->stream);
+    }
+    if (e == cudaSuccess && !out_on_device) {
+        e = cudaMemcpyAsync(images_out, dout, sizeof(float) * img_elems * n, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+    }
+    if (dvol_tmp)
+        cudaFreeAsync(dvol_tmp, c->stream);
+    if (dout_tmp)
+        cudaFreeAsync(dout_tmp, c->stream);
+    if (e != cudaSuccess)
+        return fail(c, e == cudaErrorMemoryAllocation ? BP_ENOMEM : BP_ECUDA, "bp_adjoint: %s",
+                    cudaGetErrorString(e));
+    return BP_OK;
+}

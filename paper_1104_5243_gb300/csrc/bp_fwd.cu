@@ -1,0 +1,190 @@
+// Voxel-driven cone-beam backprojection kernel (Sect. 3.1, Listing 1) for
+// sm_103a.
+//
+// For every voxel x and projection i:  (uw, vw, w) = A_i (x, 1),
+// u = uw / w, v = vw / w, VOL[x] += bilinear(I_i, u, v) / w^2, with pixels
+// outside the detector reading zero.
+//
+// GPU mapping (what differs from the paper's SSE/AVX line kernel):
+//  * Part 2 of the listing (the four scattered corner loads, the bottleneck
+//    of every SIMD variant in Sect. 4) is ONE texture gather per update: the
+//    image lives in a block-linear CUDA array, tex2Dgather returns the 2x2
+//    neighbourhood, and the border address mode supplies the zero padding of
+//    Sect. 3.3 without masks.  Interpolation weights are computed in float32
+//    here, never by the texture unit's reduced-precision filter.
+//  * The gather coordinate is the exact integer floor(u)+1: with texel
+//    centres at j + 0.5 the 2x2 footprint is then texels floor(u), floor(u)+1
+//    with no rounding in the selection.  The host folds an integer centring
+//    offset and the +1 into the matrix in float64, so the kernel works with
+//    u' = u - ku + 1, a small number whose float32 rounding error is a
+//    fraction of that of u itself, and gathers at floor(u') + ku.
+//  * One reciprocal per update (Sect. 3.3); the weight 1/w^2 is r*r.
+//  * A thread keeps 4 voxels' sums in registers over the whole batch of
+//    projections (the b-way image blocking of Sect. 6.2 with b = the batch
+//    size): the volume is read and written once per batch.  The 32 lanes of
+//    a warp take neighbouring voxels (LX along x by 32/LX along z) so one
+//    gather instruction touches a compact detector patch; each lane's 4
+//    voxels are LX apart along x, and every volume access of the warp covers
+//    whole 32-byte sectors.
+//  * The matrices and texture handles of the batch are kernel parameters,
+//    read through the constant cache with a warp-uniform index.
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "bp_internal.cuh"
+
+namespace bp {
+
+template <bool IEEE>
+__device__ __forceinline__ float recip(float w)
+{
+    if constexpr (IEEE) {
+        return __frcp_rn(w);
+    } else {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(w));
+        return r;
+    }
+}
+
+// 2x2 neighbourhood at exact integer texture coordinate (x, y):
+// returns (bl, br, tr, tl) in (.x, .y, .z, .w) -- texels (i0, j1), (i1, j1),
+// (i1, j0), (i0, j0) with i0 = x - 1, j0 = y - 1.
+template <int KIND>
+__device__ __forceinline__ float4 gather(cudaTextureObject_t t, float x, float y)
+{
+    if constexpr (KIND == kTexFloat) {
+        return tex2Dgather<float4>(t, x, y, 0);
+    } else {
+        uint4 q = tex2Dgather<uint4>(t, x, y, 0);   // raw BF16 bits, zero-extended
+        return make_float4(__uint_as_float(q.x << 16), __uint_as_float(q.y << 16),
+                           __uint_as_float(q.z << 16), __uint_as_float(q.w << 16));
+    }
+}
+
+template <int KIND, bool IEEE, int LX>
+__global__ void __launch_bounds__(kThreads)
+bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const VolGeom g,
+              int accumulate)
+{
+    constexpr int LZ = 32 / LX;                 // lanes along z
+    constexpr int TX = LX * kVoxPerLane;        // x extent of the block tile
+    const int lane = threadIdx.x & 31;
+    const int tx = lane % LX, tz = lane / LX;
+    const int L = g.L;
+    const int xb = blockIdx.x * TX + tx;        // this lane's voxels: xb + LX k
+    const int y = blockIdx.y * kWarpsY + (threadIdx.x >> 5);
+    const int z = blockIdx.z * LZ + tz;
+    if (y >= L || z >= L)
+        return;
+
+    float X[kVoxPerLane];
+#pragma unroll
+    for (int k = 0; k < kVoxPerLane; ++k)
+        X[k] = fmaf(g.R, (float)(xb + LX * k), g.Ox);
+    const float Y = fmaf(g.R, (float)y, g.Oy);
+    const float Z = fmaf(g.R, (float)z, g.Oz);
+
+    float acc[kVoxPerLane];
+#pragma unroll
+    for (int k = 0; k < kVoxPerLane; ++k)
+        acc[k] = 0.f;
+#pragma unroll 1
+    for (int i = 0; i < b.n; ++i) {
+        const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+        const float2 kc = b.k[i];
+        const cudaTextureObject_t t = b.tex[i];
+        // Part 1: geometry; the y, z terms are shared by the lane's voxels.
+        const float bu = fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w));
+        const float bv = fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w));
+        const float bw = fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w));
+#pragma unroll
+        for (int k = 0; k < kVoxPerLane; ++k) {
+            const float uw = fmaf(ru.x, X[k], bu);
+            const float vw = fmaf(rv.x, X[k], bv);
+            const float w = fmaf(rw.x, X[k], bw);
+            const float r = recip<IEEE>(w);
+            const float u = uw * r, v = vw * r;       // centred: u - ku + 1
+            const float fu0 = floorf(u), fv0 = floorf(v);
+            // Part 2: the four corners in one gather at floor(u) + 1.
+            const float4 q = gather<KIND>(t, fu0 + kc.x, fv0 + kc.y);
+            // Part 3: bilinear interpolation and the 1/w^2 weight.
+            const float fu = u - fu0, fv = v - fv0;
+            const float top = fmaf(fu, q.z - q.w, q.w);
+            const float bot = fmaf(fu, q.y - q.x, q.x);
+            const float fx = fmaf(fv, bot - top, top);
+            acc[k] = fmaf(fx, r * r, acc[k]);
+        }
+    }
+
+    float *row = vol + ((size_t)z * L + y) * L;
+#pragma unroll
+    for (int k = 0; k < kVoxPerLane; ++k) {
+        const int x = xb + LX * k;
+        if (x < L)
+            row[x] = (accumulate ? row[x] : 0.f) + acc[k];
+    }
+}
+
+template <int KIND, bool IEEE, int LX>
+static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bool acc, cudaStream_t s)
+{
+    constexpr int TX = LX * kVoxPerLane, LZ = 32 / LX;
+    dim3 grid((g.L + TX - 1) / TX, (g.L + kWarpsY - 1) / kWarpsY, (g.L + LZ - 1) / LZ);
+    bp_fwd_kernel<KIND, IEEE, LX><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int KIND, bool IEEE>
+static cudaError_t launch_kind(const FwdBatch &b, float *vol, const VolGeom &g, bool acc, int lanes_x,
+                               cudaStream_t s)
+{
+    switch (lanes_x) {
+    case 32: return launch_lx<KIND, IEEE, 32>(b, vol, g, acc, s);
+    case 16: return launch_lx<KIND, IEEE, 16>(b, vol, g, acc, s);
+    default: return launch_lx<KIND, IEEE, 8>(b, vol, g, acc, s);
+    }
+}
+
+cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int tex_kind,
+                          bool accumulate, bool ieee_rcp, int lanes_x, cudaStream_t s)
+{
+    if (b.n <= 0)
+        return cudaSuccess;
+    if (tex_kind == kTexFloat)
+        return ieee_rcp ? launch_kind<kTexFloat, true>(b, vol, g, accumulate, lanes_x, s)
+                        : launch_kind<kTexFloat, false>(b, vol, g, accumulate, lanes_x, s);
+    return ieee_rcp ? launch_kind<kTexBF16, true>(b, vol, g, accumulate, lanes_x, s)
+                    : launch_kind<kTexBF16, false>(b, vol, g, accumulate, lanes_x, s);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 images -> FP16 / BF16 arrays (round to nearest even), one thread per
+// pixel pair of a row; grid.z = image index.
+__global__ void __launch_bounds__(256)
+convert_kernel(const __grid_constant__ ConvBatch b, int isx, int isy, int to_bf16)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    const int i = blockIdx.z;
+    if (j >= isx || i >= b.n)
+        return;
+    const float f = b.src[i][(size_t)k * isx + j];
+    unsigned short bits;
+    if (to_bf16)
+        bits = __bfloat16_as_ushort(__float2bfloat16_rn(f));
+    else
+        bits = __half_as_ushort(__float2half_rn(f));
+    surf2Dwrite<unsigned short>(bits, b.surf[i], j * (int)sizeof(unsigned short), k);
+}
+
+cudaError_t launch_convert(const ConvBatch &b, int isx, int isy, int to_bf16, cudaStream_t s)
+{
+    if (b.n <= 0)
+        return cudaSuccess;
+    dim3 grid((isx + 255) / 256, isy, b.n);
+    convert_kernel<<<grid, 256, 0, s>>>(b, isx, isy, to_bf16);
+    return cudaGetLastError();
+}
+
+}  // namespace bp

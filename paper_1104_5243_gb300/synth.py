@@ -151,3 +151,14 @@ def poisson_counts(line_integrals: np.ndarray, photons: float, seed: int) -> np.
     """Poisson photon counts I ~ Poisson(I0 * exp(-l)) for each ray (float64)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.poisson(photons * np.exp(-np.asarray(line_integrals, dtype=np.float64))).astype(np.float64)
+
+
+def noisy_line_integrals(lines, photons: float, seed: int):
+    """Measured line integrals -log(max(I, 1) / I0) with photon counts
+    I ~ Poisson(I0 exp(-l)), drawn by torch on the tensor's device with a
+    generator seeded by `seed` (float32 tensor in, float32 tensor out)."""
+    import torch
+    g = torch.Generator(device=lines.device)
+    g.manual_seed(int(seed))
+    counts = torch.poisson(photons * torch.exp(-lines.double()), generator=g)
+    return (-torch.log(torch.clamp(counts, min=1.0) / photons)).float()

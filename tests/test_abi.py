@@ -1,0 +1,83 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/bp1104.h declares; argument validation that happens on the host
+before any CUDA call is checked here without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1104_5243_gb300 import _native as N
+from paper_1104_5243_gb300 import build as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bp1104.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bp_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return N.lib()
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("bp_create", "bp_add_projections", "bp_adjoint", "bp_finalize", "bp_reset",
+                 "bp_destroy", "bp_last_error", "bp_get_state", "bp_set_state"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_exactly_the_header():
+    assert sorted(N.SIGNATURES) == declared_symbols()
+
+
+def test_library_links_no_torch(lib):
+    # the ABI is plain C: the shared object must not depend on libtorch/c10
+    data = open(N.library_path(), "rb").read()
+    assert b"libtorch" not in data and b"libc10" not in data
+
+
+def test_create_rejects_bad_sizes_without_touching_the_gpu(lib):
+    h = ctypes.c_void_p()
+    O = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    for (L, R, isx, isy, dt) in [(0, 1.0, 8, 8, 0), (8, 0.0, 8, 8, 0), (8, -1.0, 8, 8, 0),
+                                 (8, 1.0, 0, 8, 0), (8, 1.0, 8, 40000, 0), (8, 1.0, 8, 8, 7)]:
+        st = lib.bp_create(ctypes.byref(h), L, R, ctypes.cast(O, ctypes.c_void_p), isx, isy, dt, None)
+        assert st == N.BP_EINVAL
+        assert h.value is None
+        assert "bp_create" in N.bp_last_error(None)
+    assert lib.bp_create(None, 8, 1.0, ctypes.cast(O, ctypes.c_void_p), 8, 8, 0, None) == N.BP_EINVAL
+
+
+def test_null_context_is_rejected(lib):
+    assert lib.bp_reset(None) == N.BP_EINVAL
+    assert lib.bp_add_projections(None, None, 0, None, 1) == N.BP_EINVAL
+    assert lib.bp_finalize(None, None, 0) == N.BP_EINVAL
+    assert lib.bp_adjoint(None, None, 0, None, 1, None, 0) == N.BP_EINVAL
+    assert lib.bp_set_option(None, 1, 0) == N.BP_EINVAL
+    assert lib.bp_destroy(None) == N.BP_OK
+
+
+def test_context_free_calls_validate_arguments(lib):
+    assert lib.bp_ramp_filter(4, 0, 1.0, None, None, None) == N.BP_EINVAL
+    assert lib.bp_ramp_filter(4, 16, -1.0, None, None, None) == N.BP_EINVAL
+    assert lib.bp_row_filter_fwd(4, 16, 0, None, None, None, None) == N.BP_EINVAL
+    assert lib.bp_row_filter_fwd(4, 16, 129, None, None, None, None) == N.BP_EINVAL
+    assert lib.bp_carm_matrices(-1, None, 785.0, 1200.0, 1.0, 0.0, 0.0, None, None) == N.BP_EINVAL
+    assert lib.bp_carm_matrices(3, None, 785.0, 1200.0, 1.0, 0.0, 0.0, None, None) == N.BP_EINVAL
+    assert lib.bp_ellipsoid_project(1, None, 8, 8, 1000, None, None, None) == N.BP_EINVAL
+    assert "bp_ellipsoid_project" in N.bp_last_error(None)
+    # empty work is a no-op that never reaches the GPU
+    assert lib.bp_ramp_filter(0, 16, 1.0, None, None, None) == N.BP_OK
+    assert lib.bp_row_filter_fwd(0, 16, 8, None, None, None, None) == N.BP_OK
+    assert lib.bp_carm_matrices(0, None, 785.0, 1200.0, 1.0, 0.0, 0.0, None, None) == N.BP_OK

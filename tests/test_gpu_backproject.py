@@ -1,0 +1,182 @@
+"""GPU parity of the backprojection (CUDA, through the C ABI) against the FP64
+oracle on seeded inputs: element by element on small and ragged cases, on
+sampled voxels at the full 512^3 x 496 x 1248x960 size, plus the storage
+forms, options, streaming, checkpoint/resume and edge cases.
+
+Tolerances (stated per case): FP32 path rel-L2 <= 1e-5 against the oracle;
+FP16 storage <= 1e-3; BF16 storage reported with a loose bound (8 mantissa
+bits give about 2e-3 per pixel)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1104_5243_gb300 import synth
+
+from gpu_common import native, rel_l2, tiny_phantom_case, torch
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL, FP16_TOL, BF16_TOL = 1e-5, 1e-3, 1e-2
+
+
+def run_gpu(vol, scan, A, q, dtype="f32", batch=None, ieee=False, on_device=True, chunks=None):
+    api = native()
+    from paper_1104_5243_gb300 import _native as N
+    bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype)
+    if batch is not None:
+        bp.set_option(N.BP_OPT_BATCH, batch)
+    if ieee:
+        bp.set_option(N.BP_OPT_IEEE_RCP, 1)
+    qt = torch.from_numpy(np.ascontiguousarray(q))
+    qt = qt.cuda() if on_device else qt.pin_memory()
+    bounds = chunks or [(0, A.shape[0])]
+    for (a, b) in bounds:
+        bp.add_projections(qt[a:b], A[a:b])
+    out = bp.finalize().cpu().numpy()
+    bp.close()
+    return out
+
+
+def test_tiny_phantom_fp32_matches_oracle():
+    scan, vol, A, ell, q, ref = tiny_phantom_case()
+    got = run_gpu(vol, scan, A, q)
+    err = rel_l2(got, ref)
+    print(f"tiny fp32 rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e} PSNR {oracle.psnr(got, ref):.1f} dB")
+    assert err <= FP32_TOL
+
+
+@pytest.mark.parametrize("dtype,tol", [("f16", FP16_TOL), ("bf16", BF16_TOL)])
+def test_tiny_phantom_16bit_storage(dtype, tol):
+    scan, vol, A, ell, q, ref = tiny_phantom_case()
+    got = run_gpu(vol, scan, A, q, dtype=dtype)
+    err = rel_l2(got, ref)
+    print(f"tiny {dtype} rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e} PSNR {oracle.psnr(got, ref):.1f} dB")
+    assert err <= tol
+
+
+def test_ieee_reciprocal_option():
+    scan, vol, A, ell, q, ref = tiny_phantom_case()
+    got = run_gpu(vol, scan, A, q, ieee=True)
+    assert rel_l2(got, ref) <= FP32_TOL
+
+
+@pytest.mark.parametrize("L,isx,isy,n,batch", [
+    (37, 53, 41, 70, None),     # ragged volume/detector, two passes
+    (40, 160, 120, 9, 4),       # L % 4 == 0 but not a tile multiple, small batches
+    (1, 7, 5, 3, None),         # single voxel
+])
+def test_ragged_sizes_random_data(L, isx, isy, n, batch):
+    scan = synth.Scan(n=n, isx=isx, isy=isy, pitch=384.0 / isx)
+    vol = synth.Volume(L)
+    A = oracle.carm_matrices(scan)
+    q = np.random.default_rng(L + n).standard_normal((n, isy, isx)).astype(np.float32)
+    ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
+    got = run_gpu(vol, scan, A, q, batch=batch)
+    assert rel_l2(got, ref) <= FP32_TOL
+
+
+def test_detector_smaller_than_volume_zero_padding():
+    """A detector that sees only part of the volume: voxels projecting outside
+    must read zero (Sect. 3.3 padding), checked element by element."""
+    scan = synth.Scan(n=20, isx=24, isy=10, pitch=4.0)
+    vol = synth.Volume(32)
+    A = oracle.carm_matrices(scan)
+    q = np.random.default_rng(3).random((scan.n, scan.isy, scan.isx), dtype=np.float32) + 0.5
+    ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
+    got = run_gpu(vol, scan, A, q)
+    assert (ref == 0).sum() > 1000
+    np.testing.assert_array_equal(got[ref == 0], 0.0)
+    assert rel_l2(got, ref) <= FP32_TOL
+
+
+def test_batch_size_and_chunking_do_not_change_the_result():
+    scan, vol, A, ell, q, ref = tiny_phantom_case()
+    a = run_gpu(vol, scan, A, q)
+    b = run_gpu(vol, scan, A, q, batch=5, chunks=[(0, 11), (11, 12), (12, 36)])
+    assert rel_l2(b, ref) <= FP32_TOL
+    assert rel_l2(a, b) <= 1e-6
+
+
+def test_host_and_device_inputs_are_bit_identical():
+    scan, vol, A, ell, q, ref = tiny_phantom_case()
+    for dtype in ("f32", "f16"):
+        a = run_gpu(vol, scan, A, q, dtype=dtype, on_device=True)
+        b = run_gpu(vol, scan, A, q, dtype=dtype, on_device=False)
+        np.testing.assert_array_equal(a, b)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    api = native()
+    scan, vol, A, ell, q, ref = tiny_phantom_case()
+    qt = torch.from_numpy(q).cuda()
+    one = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
+    one.add_projections(qt[:20], A[:20])
+    one.add_projections(qt[20:], A[20:])
+    full = one.finalize().cpu()
+    two = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
+    two.add_projections(qt[:20], A[:20])
+    state, n = two.get_state()
+    assert n == 20
+    two.close()
+    three = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
+    three.set_state(state.cpu(), n)
+    three.add_projections(qt[20:], A[20:])
+    resumed = three.finalize().cpu()
+    assert three.get_state()[1] == 36
+    assert torch.equal(full, resumed)
+
+
+def test_reset_and_empty_batch():
+    api = native()
+    scan, vol, A, ell, q, ref = tiny_phantom_case()
+    bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
+    qt = torch.from_numpy(q).cuda()
+    bp.add_projections(qt, A)
+    bp.reset()
+    bp.add_projections(qt[:0], A[:0])
+    assert float(bp.finalize().abs().max()) == 0.0
+    bp.add_projections(qt, A)
+    assert rel_l2(bp.finalize().cpu().numpy(), ref) <= FP32_TOL
+
+
+def test_volume_behind_source_is_rejected():
+    api = native()
+    from paper_1104_5243_gb300 import _native as N
+    scan = synth.Scan(n=2, isx=16, isy=16, pitch=20.0, sid=100.0, sdd=200.0)
+    vol = synth.Volume(16)
+    A = oracle.carm_matrices(scan)      # source inside the 256 mm volume
+    bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
+    with pytest.raises(N.BpError) as e:
+        bp.add_projections(torch.zeros((2, 16, 16), device="cuda"), A)
+    assert e.value.status == N.BP_EINVAL
+    with pytest.raises(N.BpError):
+        bp.add_projections(torch.zeros((2, 16, 16), device="cuda"), A * np.nan)
+
+
+def test_gpu_matrices_match_oracle():
+    api = native()
+    for name in ("tiny", "full", "train"):
+        scan = synth.SCANS[name]
+        np.testing.assert_allclose(api.carm_matrices(scan), oracle.carm_matrices(scan), rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("L,dtype,tol", [(512, "f32", FP32_TOL), (512, "f16", FP16_TOL)])
+def test_full_size_sampled_voxels(L, dtype, tol):
+    """512^3 x 496 x 1248x960, uniform timing stack, in the launch
+    configuration the benchmark times (batches of 64, device input); the
+    oracle evaluates 4096 sampled voxels one by one."""
+    api = native()
+    scan, vol = synth.SCANS["full"], synth.Volume(L)
+    A = oracle.carm_matrices(scan)
+    stack = synth.uniform_stack(scan.n, scan.isy, scan.isx)
+    bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype)
+    bp.add_projections(torch.from_numpy(stack).cuda(), A)
+    got = bp.finalize().view(-1)
+    rng = np.random.default_rng(7)
+    idx = rng.integers(0, L ** 3, size=4096)
+    ref = oracle.backproject_voxels(vol.L, vol.R, vol.O, stack, A, idx)
+    g = got[torch.from_numpy(idx).cuda()].cpu().numpy()
+    err = rel_l2(g, ref)
+    print(f"{L}^3 {dtype} sampled rel-L2 {err:.3e} max-rel {np.max(np.abs(g - ref) / np.maximum(np.abs(ref), 1e-30)):.3e}")
+    assert err <= tol
+    bp.close()
