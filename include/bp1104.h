@@ -208,6 +208,24 @@ bp_status bp_row_filter_fwd(long long rows, int isx, int T, const float *h, cons
 bp_status bp_row_filter_bwd(long long rows, int isx, int T, const float *h, const float *in,
                             const float *g, float *gin, float *gh, void *stream);
 
+/* Allocation-free form of bp_row_filter_bwd (the paper has no counterpart:
+ * this serves callers of the library, not the method).  Same arguments and
+ * results (gh summed in a different but fixed order, so within float32
+ * rounding of bp_row_filter_bwd's, and deterministic), for callers that must
+ * not allocate device memory once running -- e.g. a reconstruction loop that
+ * budgets all device memory at start-up, or a host framework whose allocator
+ * owns the device.  Its scratch is a fixed 128 KiB device array inside the
+ * library (256 blocks x 128 taps of float32), held by every GPU that loads
+ * the library until the process exits; T above 128 is rejected with
+ * BP_EINVAL.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (e.g. on
+ * two streams) race and must be serialised by the caller.  Makes no call to
+ * cudaMalloc, cudaMallocAsync or cudaFree. */
+bp_status bp_row_filter_bwd_noalloc(long long rows, int isx, int T, const float *h,
+                                    const float *in, const float *g, float *gin, float *gh,
+                                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

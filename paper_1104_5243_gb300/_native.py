@@ -35,6 +35,7 @@ SIGNATURES = {
     "bp_ramp_filter": (_i, [_ll, _i, _d, _vp, _vp, _vp]),
     "bp_row_filter_fwd": (_i, [_ll, _i, _i, _vp, _vp, _vp, _vp]),
     "bp_row_filter_bwd": (_i, [_ll, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "bp_row_filter_bwd_noalloc": (_i, [_ll, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lock = threading.Lock()
@@ -166,3 +167,9 @@ def bp_row_filter_fwd(rows, isx, T, h_ptr, in_ptr, out_ptr, stream=None):
 def bp_row_filter_bwd(rows, isx, T, h_ptr, in_ptr, g_ptr, gin_ptr, gh_ptr, stream=None):
     check(lib().bp_row_filter_bwd(int(rows), int(isx), int(T), h_ptr, in_ptr, g_ptr, gin_ptr, gh_ptr,
                                   stream))
+
+
+def bp_row_filter_bwd_noalloc(rows, isx, T, h_ptr, in_ptr, g_ptr, gin_ptr, gh_ptr, stream=None):
+    """Same as bp_row_filter_bwd, with fixed in-library scratch (no allocation)."""
+    check(lib().bp_row_filter_bwd_noalloc(int(rows), int(isx), int(T), h_ptr, in_ptr, g_ptr, gin_ptr,
+                                          gh_ptr, stream))
