@@ -33,31 +33,52 @@ sys.path.insert(0, ROOT)
 METRIC = "GUP/s at 512³×496 proj: FP32 vs FP16-projection form, % of roofline"
 UNIT = "GUP/s"
 
-# GB300 unit counts used for the roofline (per SM per clock):
-#   texture gathers: 4 quad-texel (tld4) results per SM per clock (one per
-#     texture unit, 4 texture units per SM);
-#   FP32 lanes: 128 per SM per clock; the kernel issues 18.5 FP32-pipe
-#     instructions per update (counted from its source: 3 FFMA geometry,
-#     2 FMUL u/v, 2 floor, 2 FADD fractions, 3 FADD + 3 FFMA interpolation,
-#     1 FMUL + 1 FFMA weight/accumulate, plus 6 FFMA per 4 voxels for the
-#     y/z terms);
-#   MUFU reciprocal: 16 per SM per clock.
-SMS = 152
-GATHER_PER_SM_CLK = 4.0
+# Roofline of the backprojection kernel (one update = one voxel x one
+# projection), per SM per clock, times SMs and the SM clock sampled under load:
+#   gather: the texture unit's 2x2-gather rate for the storage type, MEASURED
+#     on this GPU by bp_probe_gather (one gather per update);
+#   fp32_issue: 128 FP32 lanes per SM per clock over the kernel's 20.5 FP32-pipe
+#     instructions per update (from its source: 3 FFMA geometry + 1.5 FFMA of
+#     y/z terms per 4 voxels, 2 FMUL u/v, 2 floor, 2 FADD gather coordinate,
+#     2 FADD fractions, 3 FADD + 3 FFMA interpolation, 1 FMUL + 1 FFMA weight
+#     and accumulate);
+#   mufu: 16 reciprocals per SM per clock, one per update.
 FP32_PER_SM_CLK = 128.0
-FP32_INSTR_PER_UPDATE = 18.5
+FP32_INSTR_PER_UPDATE = 20.5
 MUFU_PER_SM_CLK = 16.0
 
 
-def roofline_peak_gups(sm_mhz: float, sms: int = SMS) -> dict:
+def roofline_peak_gups(sm_mhz: float, sms: int, gather_per_sm_clk: float) -> dict:
     f = sm_mhz * 1e6
     bounds = {
-        "gather": sms * GATHER_PER_SM_CLK * f / 1e9,
+        "gather": sms * gather_per_sm_clk * f / 1e9,
         "fp32_issue": sms * FP32_PER_SM_CLK / FP32_INSTR_PER_UPDATE * f / 1e9,
         "mufu": sms * MUFU_PER_SM_CLK * f / 1e9,
     }
     bounds["min"] = min(bounds.values())
     return bounds
+
+
+def ncu_traffic(kernel_file: str, profile: str):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    summary is missing or the kernel source changed since it was captured."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        src = open(os.path.join(ROOT, "paper_1104_5243_gb300", "csrc", kernel_file), "rb").read()
+    except OSError:
+        return None
+    fields = {}
+    for ln in text.splitlines():
+        if ":" in ln and ln.strip().startswith(("traffic_bytes_per_launch", "source_sha256")):
+            k, v = ln.split(":", 1)
+            fields[k.strip("-* `")] = v.strip().strip("`")
+    if fields.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    try:
+        return float(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 # ---------------------------------------------------------------------------
@@ -156,22 +177,24 @@ def cpu_baseline(L: int, n_sample: int):
 
 
 def run_reference(args, rank: int):
+    """Reference arm: the FP64 oracle (there is no reference implementation
+    of the paper's code) on the host cores, each step a bounded sample of the
+    512^3 x 496 workload: the full volume from --ref-proj projections."""
     if rank != 0:
         return
-    cb = cpu_baseline(args.L, args.cpu_proj)
-    steps = []
-    for _ in range(args.steps):
-        c = cpu_baseline(args.L, args.ref_proj) if args.ref_proj != args.cpu_proj else cb
-        steps.append(c["value"])
-    value = statistics.median(steps)
+    for _ in range(args.warmup):
+        cpu_baseline(args.L, max(1, args.ref_proj // 8))
+    samples = [cpu_baseline(args.L, args.ref_proj) for _ in range(args.steps)]
+    value = statistics.median(c["value"] for c in samples)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"backprojection {args.L}^3 x 496 x 1248x960 (bounded sample)",
+        "config": {"workload": f"FDK backprojection {args.L}^3 x 496 x 1248x960, uniform [0,1) stack seed "
+                               "20110426, 200-degree C-arm (bounded sample per step)",
                    "L": args.L, "n_proj": 496, "detector": [1248, 960]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                         "sample": cb["sample"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[0]["cores"], "kind": "oracle",
+                         "sample": samples[0]["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -186,8 +209,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--L", type=int, default=512)
     ap.add_argument("--forms", default="f32,f16,bf16")
-    ap.add_argument("--cpu-proj", type=int, default=16, help="projections in the oracle sample")
-    ap.add_argument("--ref-proj", type=int, default=16)
+    ap.add_argument("--n-proj", type=int, default=496, help="projections per step (profiling runs)")
+    ap.add_argument("--cpu-proj", type=int, default=128, help="projections in the oracle sample")
+    ap.add_argument("--ref-proj", type=int, default=48, help="projections per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -215,7 +239,10 @@ def main():
     from paper_1104_5243_gb300 import _native as N
     from paper_1104_5243_gb300 import api, synth
 
-    scan, vol = synth.SCANS["full"], synth.Volume(args.L)
+    full = synth.SCANS["full"]
+    scan = synth.Scan(n=args.n_proj, isx=full.isx, isy=full.isy, pitch=full.pitch,
+                      scan_deg=full.scan_deg * (args.n_proj - 1) / (full.n - 1))
+    vol = synth.Volume(args.L)
     A = api.carm_matrices(scan)                         # FP64 on the GPU
     stack_host = torch.from_numpy(synth.uniform_stack(scan.n, scan.isy, scan.isx)).pin_memory()
     stack = stack_host.cuda()
@@ -236,6 +263,9 @@ def main():
         return float(t.item())
 
     smi_id = gpu_id_for_smi(torch, local_rank)
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    gather_rate = {f: N.bp_probe_gather({"f32": N.BP_F32, "f16": N.BP_F16, "bf16": N.BP_BF16}[f])
+                   for f in args.forms.split(",")}
     forms = {}
     kernel = {}
     clocks = None
@@ -301,21 +331,27 @@ def main():
             dist.destroy_process_group()
         return
 
-    f32 = forms.get("f32") or next(iter(forms.values()))
+    head = "f32" if "f32" in forms else next(iter(forms))
+    f32 = forms[head]
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    peak = roofline_peak_gups(sm_mhz)
-    k = kernel.get("f32") or next(iter(kernel.values()))
+    peaks = {f: roofline_peak_gups(sm_mhz, sms, gather_rate[f]) for f in forms}
+    peak = peaks[head]
+    k = kernel[head]
     achieved = k["kernel_gups"]
+    traffic = ncu_traffic("bp_fwd.cu", f"bp_fwd_kernel_{head}_{args.L}.md") if args.n_proj == 496 else None
     roofline = {
-        "bound": "alu", "unit": UNIT, "kernel": "bp_fwd_kernel (FP32 projections)",
+        "bound": "alu", "unit": UNIT, "kernel": f"bp_fwd_kernel ({head} projections)",
         "achieved": round(achieved, 2) if achieved else None,
         "peak": round(peak["min"], 1),
         "frac": round(achieved / peak["min"], 4) if achieved else None,
+        "peak_basis": "min(measured texture gather rate, FP32 issue, MUFU) x SMs x sampled SM clock",
         "peak_at_sm_mhz": sm_mhz,
+        "gather_per_sm_clk_measured": {f: round(v, 3) for f, v in gather_rate.items()},
         "bounds_gups": {kk: round(v, 1) for kk, v in peak.items()},
         "avg_launch_ms": round(k["kernel_ms"] / max(k["launches"], 1), 4),
         "launches": k["launches"],
-        "traffic": None,
+        "traffic": traffic,
+        "algorithmic_bytes_per_launch": int(vol.L ** 3 * 8 + min(scan.n, 64) * scan.isx * scan.isy * 4),
     }
     cpu = None
     if not args.no_cpu_baseline:
@@ -325,18 +361,24 @@ def main():
         "warmup": args.warmup, "ms_per_step": f32["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"FDK backprojection {args.L}^3 x {scan.n} x {scan.isx}x{scan.isy}, "
-                               "uniform [0,1) stack seed 20110426, 200-degree C-arm",
+                               f"uniform [0,1) stack seed 20110426, {scan.scan_deg:.0f}-degree C-arm",
                    "L": args.L, "n_proj": scan.n, "detector": [scan.isx, scan.isy],
                    "l2": "inputs larger than L2 (2.38 GB projections + 0.54 GB volume per step)",
                    "step": "reset + bp_add_projections(496, device-resident) + finalize"},
-        "forms": {kk: {**v, "frac_of_roofline": round(v["value"] / world / peak["min"], 4)}
+        "forms": {kk: {**v, "kernel_gups": round(kernel[kk]["kernel_gups"], 2),
+                       "frac_of_roofline": round(kernel[kk]["kernel_gups"] / peaks[kk]["min"], 4),
+                       "roofline_gups": round(peaks[kk]["min"], 1)}
                   for kk, v in forms.items()},
+        "fp16_vs_fp32": (round(forms["f16"]["value"] / forms["f32"]["value"], 3)
+                         if "f16" in forms and "f32" in forms else None),
         "kernel_events": {kk: {"launches": v["launches"], "kernel_ms": round(v["kernel_ms"], 3)}
                           for kk, v in kernel.items()},
         "roofline": roofline,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": sum(v["launches"] for v in kernel.values()),
+        # backprojection kernels, plus one FP32->16-bit conversion kernel per
+        # batch for the 16-bit forms
+        "gpu_launches": sum(v["launches"] * (1 if kk == "f32" else 2) for kk, v in kernel.items()),
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

@@ -70,9 +70,10 @@ typedef enum {
     /* 1: record a CUDA event pair around every backprojection kernel launch
      * on the context's stream, for bp_kernel_stats; 0 (default): off. */
     BP_OPT_TIMING = 3,
-    /* Warp layout of the backprojection kernel: lanes along x (8, 16 or 32;
-     * the rest along z).  Default 8.  Changes speed, not results beyond
-     * float32 summation order. */
+    /* Warp layout of the backprojection kernel: 8, 16 or 32 lanes along x
+     * (the rest along z), or a two-digit code XY = X lanes along x by Y along
+     * y (44, 42, 82, 24; the rest along z).  Default 8.  Changes speed only:
+     * every voxel still sums its projections in the same order. */
     BP_OPT_LANES_X = 4
 } bp_option;
 
@@ -146,6 +147,16 @@ bp_status bp_adjoint(bp_ctx *ctx, const float *vol, int vol_on_device,
  * number of launches and their summed CUDA-event time in ms, and clears the
  * record.  Either output pointer may be NULL. */
 bp_status bp_kernel_stats(bp_ctx *ctx, long long *launches, double *total_ms);
+
+/* Measured speed of light of Part 2 of Listing 1 (Sect. 3.1) on this GPU:
+ * the texture unit's 2x2-gather rate for projections stored as `dtype`, in
+ * gathers per SM per clock, with the backprojection kernel's warp shape
+ * (lanes on neighbouring pixels) and an L1-resident footprint.  The paper
+ * bases its bounds on measured machine figures (Sect. 2, Table 1; Sect. 3.2);
+ * this is the GPU counterpart used for the roofline.  Synchronous (runs a
+ * short kernel on the current device, allocating and freeing a 256 x 256
+ * array). */
+bp_status bp_probe_gather(bp_dtype dtype, double *gathers_per_sm_clk);
 
 /* Message of the last failure on ctx (or, for ctx == NULL, of the calling
  * thread's last failing context-free call).  Never NULL. */

@@ -27,6 +27,7 @@ SIGNATURES = {
     "bp_set_state": (_i, [_vp, _vp, _i, _ll]),
     "bp_adjoint": (_i, [_vp, _vp, _i, _vp, _i, _vp, _i]),
     "bp_kernel_stats": (_i, [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_d)]),
+    "bp_probe_gather": (_i, [_i, ctypes.POINTER(_d)]),
     "bp_last_error": (ctypes.c_char_p, [_vp]),
     "bp_carm_matrices": (_i, [_i, _vp, _d, _d, _d, _d, _d, _vp, _vp]),
     "bp_ellipsoid_project": (_i, [_i, _vp, _i, _i, _i, _vp, _vp, _vp]),
@@ -128,6 +129,13 @@ def bp_kernel_stats(ctx):
     n, ms = _ll(0), _d(0.0)
     check(lib().bp_kernel_stats(ctx, ctypes.byref(n), ctypes.byref(ms)), ctx)
     return n.value, ms.value
+
+
+def bp_probe_gather(dtype) -> float:
+    """Texture 2x2-gather rate (gathers per SM per clock) for a storage type."""
+    r = _d(0.0)
+    check(lib().bp_probe_gather(int(dtype), ctypes.byref(r)))
+    return r.value
 
 
 def bp_last_error(ctx=None) -> str:

@@ -113,8 +113,7 @@ static bp_status alloc_slot(bp_ctx *c, int s, int j)
         fmt = cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindFloat);
     else
         fmt = cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
-    const unsigned flags = c->dtype == BP_F32 ? cudaArrayDefault : cudaArraySurfaceLoadStore;
-    CTX_CK(c, cudaMallocArray(&c->arr[s][j], &fmt, c->isx, c->isy, flags));
+    CTX_CK(c, cudaMallocArray(&c->arr[s][j], &fmt, c->isx, c->isy, cudaArraySurfaceLoadStore));
     cudaResourceDesc res;
     memset(&res, 0, sizeof res);
     res.resType = cudaResourceTypeArray;
@@ -127,8 +126,7 @@ static bp_status alloc_slot(bp_ctx *c, int s, int j)
     td.readMode = cudaReadModeElementType;
     td.normalizedCoords = 0;
     CTX_CK(c, cudaCreateTextureObject(&c->tex[s][j], &res, &td, nullptr));
-    if (c->dtype != BP_F32)
-        CTX_CK(c, cudaCreateSurfaceObject(&c->surf[s][j], &res));
+    CTX_CK(c, cudaCreateSurfaceObject(&c->surf[s][j], &res));
     return BP_OK;
 }
 
@@ -221,8 +219,8 @@ extern "C" bp_status bp_set_option(bp_ctx *c, int option, long long value)
         c->batch = (int)value;
         return BP_OK;
     case BP_OPT_LANES_X:
-        if (value != 8 && value != 16 && value != 32)
-            return fail(c, BP_EINVAL, "bp_set_option: LANES_X takes 8, 16 or 32");
+        if (value != 8 && value != 16 && value != 32 && value != 44 && value != 42 && value != 82 && value != 24)
+            return fail(c, BP_EINVAL, "bp_set_option: LANES_X takes 8, 16, 32, 44, 42, 82 or 24");
         c->lanes_x = (int)value;
         return BP_OK;
     case BP_OPT_TIMING:
@@ -330,7 +328,8 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
         c->next_set ^= 1;
         CTX_CK(c, cudaStreamWaitEvent(c->copy_stream, c->kern_done[s], 0));
         const float *src0 = images + (size_t)c0 * img_elems;
-        if (c->dtype == BP_F32) {
+        if (c->dtype == BP_F32 && !images_on_device) {
+            // host images go straight into the arrays on the copy engine
             for (int j = 0; j < m; ++j)
                 CTX_CK(c, cudaMemcpy2DToArrayAsync(c->arr[s][j], 0, 0, src0 + (size_t)j * img_elems, row_bytes,
                                                    row_bytes, c->isy, kind, c->copy_stream));
@@ -349,7 +348,8 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 cb.src[j] = src + (size_t)j * img_elems;
                 cb.surf[j] = c->surf[s][j];
             }
-            CTX_CK(c, launch_convert(cb, c->isx, c->isy, c->dtype == BP_BF16, c->copy_stream));
+            const int mode = c->dtype == BP_F32 ? 0 : c->dtype == BP_F16 ? 1 : 2;
+            CTX_CK(c, launch_convert(cb, c->isx, c->isy, mode, c->copy_stream));
         }
         CTX_CK(c, cudaEventRecord(c->copy_done[s], c->copy_stream));
         CTX_CK(c, cudaStreamWaitEvent(c->stream, c->copy_done[s], 0));

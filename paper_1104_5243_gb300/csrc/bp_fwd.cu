@@ -62,18 +62,18 @@ __device__ __forceinline__ float4 gather(cudaTextureObject_t t, float x, float y
     }
 }
 
-template <int KIND, bool IEEE, int LX>
-__global__ void __launch_bounds__(kThreads)
+template <int KIND, bool IEEE, int LX, int LY>
+__global__ void __launch_bounds__(kThreads, 6)
 bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const VolGeom g,
               int accumulate)
 {
-    constexpr int LZ = 32 / LX;                 // lanes along z
+    constexpr int LZ = 32 / (LX * LY);          // lanes along z
     constexpr int TX = LX * kVoxPerLane;        // x extent of the block tile
     const int lane = threadIdx.x & 31;
-    const int tx = lane % LX, tz = lane / LX;
+    const int tx = lane % LX, ty = (lane / LX) % LY, tz = lane / (LX * LY);
     const int L = g.L;
     const int xb = blockIdx.x * TX + tx;        // this lane's voxels: xb + LX k
-    const int y = blockIdx.y * kWarpsY + (threadIdx.x >> 5);
+    const int y = (blockIdx.y * kWarpsY + (threadIdx.x >> 5)) * LY + ty;
     const int z = blockIdx.z * LZ + tz;
     if (y >= L || z >= L)
         return;
@@ -126,23 +126,30 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
     }
 }
 
-template <int KIND, bool IEEE, int LX>
+template <int KIND, bool IEEE, int LX, int LY>
 static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bool acc, cudaStream_t s)
 {
-    constexpr int TX = LX * kVoxPerLane, LZ = 32 / LX;
-    dim3 grid((g.L + TX - 1) / TX, (g.L + kWarpsY - 1) / kWarpsY, (g.L + LZ - 1) / LZ);
-    bp_fwd_kernel<KIND, IEEE, LX><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0);
+    constexpr int TX = LX * kVoxPerLane, TY = kWarpsY * LY, LZ = 32 / (LX * LY);
+    dim3 grid((g.L + TX - 1) / TX, (g.L + TY - 1) / TY, (g.L + LZ - 1) / LZ);
+    bp_fwd_kernel<KIND, IEEE, LX, LY><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0);
     return cudaGetLastError();
 }
 
+// Warp layouts (bp_set_option BP_OPT_LANES_X): 8, 16, 32 = lanes along x
+// (the rest along z); two-digit codes XY = X lanes along x by Y along y
+// (the rest along z): 44, 42, 82, 24.
 template <int KIND, bool IEEE>
-static cudaError_t launch_kind(const FwdBatch &b, float *vol, const VolGeom &g, bool acc, int lanes_x,
+static cudaError_t launch_kind(const FwdBatch &b, float *vol, const VolGeom &g, bool acc, int layout,
                                cudaStream_t s)
 {
-    switch (lanes_x) {
-    case 32: return launch_lx<KIND, IEEE, 32>(b, vol, g, acc, s);
-    case 16: return launch_lx<KIND, IEEE, 16>(b, vol, g, acc, s);
-    default: return launch_lx<KIND, IEEE, 8>(b, vol, g, acc, s);
+    switch (layout) {
+    case 32: return launch_lx<KIND, IEEE, 32, 1>(b, vol, g, acc, s);
+    case 16: return launch_lx<KIND, IEEE, 16, 1>(b, vol, g, acc, s);
+    case 44: return launch_lx<KIND, IEEE, 4, 4>(b, vol, g, acc, s);
+    case 42: return launch_lx<KIND, IEEE, 4, 2>(b, vol, g, acc, s);
+    case 82: return launch_lx<KIND, IEEE, 8, 2>(b, vol, g, acc, s);
+    case 24: return launch_lx<KIND, IEEE, 2, 4>(b, vol, g, acc, s);
+    default: return launch_lx<KIND, IEEE, 8, 1>(b, vol, g, acc, s);
     }
 }
 
@@ -159,10 +166,12 @@ cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int t
 }
 
 // ---------------------------------------------------------------------------
-// FP32 images -> FP16 / BF16 arrays (round to nearest even), one thread per
-// pixel pair of a row; grid.z = image index.
+// FP32 images -> projection arrays: copied as float32 (MODE 0) or rounded to
+// FP16 (1) / BF16 (2) with round-to-nearest-even, written through surfaces
+// into the block-linear arrays; one thread per pixel, grid.z = image index.
+template <int MODE>
 __global__ void __launch_bounds__(256)
-convert_kernel(const __grid_constant__ ConvBatch b, int isx, int isy, int to_bf16)
+convert_kernel(const __grid_constant__ ConvBatch b, int isx, int isy)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
@@ -170,20 +179,26 @@ convert_kernel(const __grid_constant__ ConvBatch b, int isx, int isy, int to_bf1
     if (j >= isx || i >= b.n)
         return;
     const float f = b.src[i][(size_t)k * isx + j];
-    unsigned short bits;
-    if (to_bf16)
-        bits = __bfloat16_as_ushort(__float2bfloat16_rn(f));
-    else
-        bits = __half_as_ushort(__float2half_rn(f));
-    surf2Dwrite<unsigned short>(bits, b.surf[i], j * (int)sizeof(unsigned short), k);
+    if constexpr (MODE == 0) {
+        surf2Dwrite<float>(f, b.surf[i], j * (int)sizeof(float), k);
+    } else {
+        const unsigned short bits = MODE == 2 ? __bfloat16_as_ushort(__float2bfloat16_rn(f))
+                                              : __half_as_ushort(__float2half_rn(f));
+        surf2Dwrite<unsigned short>(bits, b.surf[i], j * (int)sizeof(unsigned short), k);
+    }
 }
 
-cudaError_t launch_convert(const ConvBatch &b, int isx, int isy, int to_bf16, cudaStream_t s)
+cudaError_t launch_convert(const ConvBatch &b, int isx, int isy, int mode, cudaStream_t s)
 {
     if (b.n <= 0)
         return cudaSuccess;
     dim3 grid((isx + 255) / 256, isy, b.n);
-    convert_kernel<<<grid, 256, 0, s>>>(b, isx, isy, to_bf16);
+    if (mode == 0)
+        convert_kernel<0><<<grid, 256, 0, s>>>(b, isx, isy);
+    else if (mode == 2)
+        convert_kernel<2><<<grid, 256, 0, s>>>(b, isx, isy);
+    else
+        convert_kernel<1><<<grid, 256, 0, s>>>(b, isx, isy);
     return cudaGetLastError();
 }
 

@@ -59,13 +59,14 @@ cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int t
 cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom &g,
                               float *out, int isx, int isy, bool ieee_rcp, cudaStream_t s);
 
-// FP32 -> FP16 / BF16 conversion of up to kMaxBatch images into surfaces.
+// Copy (mode 0) or FP16 (1) / BF16 (2) conversion of up to kMaxBatch FP32
+// images into the projection arrays' surfaces.
 struct ConvBatch {
     const float *src[kMaxBatch];
     cudaSurfaceObject_t surf[kMaxBatch];
     int n;
 };
-cudaError_t launch_convert(const ConvBatch &b, int isx, int isy, int to_bf16, cudaStream_t s);
+cudaError_t launch_convert(const ConvBatch &b, int isx, int isy, int mode, cudaStream_t s);
 
 // Thread-local message for context-free entry points.
 void set_thread_error(const char *fmt, ...);

@@ -7,12 +7,15 @@
 * ``RowFilterFn``: the short per-row convolution with T taps; backward runs
   the row-filter gradient kernel (input gradient and a deterministic
   two-pass tap reduction).
-* ``LearnedRowFilter``: T learned taps (default 64) that replace the Ram-Lak
-  ramp in the 2-D FDK pre-processing (Sect. 1.1 names the step; the cosine
-  and Parker weights stay fixed).  Initialised to the truncated Ram-Lak
-  kernel, trained on phantoms this package projects itself, judged against
-  the phantom and against the plain ramp-filter FDK, which stays available
-  as the fallback (``ramp_fdk``).
+* ``LearnedRowFilter``: T learned taps (default 64) that replace the central
+  T taps of the Ram-Lak ramp in the 2-D FDK pre-processing (Sect. 1.1 names
+  the step; the cosine and Parker weights stay fixed).  The ramp's tails
+  beyond +-T/2 pixels stay analytic: they carry the |omega| response at low
+  frequencies, which no short filter can represent, and no noise trade-off.
+  Initialised to the Ram-Lak kernel (so training starts from the plain
+  FDK), trained on phantoms this package projects itself, judged against the
+  phantom and against the plain ramp-filter FDK, which stays available as
+  the fallback (``ramp_fdk``).
 
 Every computation on the data path runs in libbp1104.so; PyTorch provides the
 tensors, the autograd tape, the loss and the optimiser.
@@ -79,14 +82,42 @@ def ramlak_taps(T: int, tau: float, scale: float = 1.0) -> np.ndarray:
 
 
 class LearnedRowFilter(torch.nn.Module):
-    """T learned taps applied along every detector row."""
+    """The ramp filter with its central T taps learned:
+    q = ramp(x) + (taps - ramlak_central) * x along every detector row, where
+    ramp is the full-length Ram-Lak filter at isocenter pitch tau.
 
-    def __init__(self, T: int = 64, tau: float = 1.0, scale: float = 1.0):
+    The learned change of the taps is symmetric and parameterised by its
+    frequency response: delta(m) = sum_k coef[k] cos(2 pi k m / T) for the
+    T/2 + 1 frequencies k (the "response" form of the learned filter).  Each
+    parameter then moves one frequency band, which keeps the optimisation
+    well conditioned: in the tap basis the low-frequency (DC) direction,
+    to which the reconstruction error is by far most sensitive, dominates
+    every tap's gradient."""
+
+    def __init__(self, T: int = 64, tau: float = 1.0):
         super().__init__()
-        self.taps = torch.nn.Parameter(torch.from_numpy(ramlak_taps(T, tau, scale)))
+        self.tau = float(tau)
+        central = torch.from_numpy(ramlak_taps(T, tau))
+        m = torch.arange(T, dtype=torch.float64) - T // 2
+        k = torch.arange(T // 2 + 1, dtype=torch.float64)
+        basis = torch.cos(2.0 * math.pi * m[:, None] * k[None, :] / T).float()
+        self.coef = torch.nn.Parameter(torch.zeros(T // 2 + 1))
+        self.register_buffer("ramlak_central", central)
+        self.register_buffer("basis", basis)
+
+    @property
+    def delta(self) -> torch.Tensor:
+        return self.basis @ self.coef
+
+    @property
+    def taps(self) -> torch.Tensor:
+        """The learned central taps (Ram-Lak central taps + learned change)."""
+        return self.ramlak_central + self.delta
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
-        return row_filter(x, self.taps)
+        with torch.no_grad():
+            base = api.ramp_filter(x, self.tau)
+        return base + row_filter(x, self.delta.contiguous())
 
 
 # ---------------------------------------------------------------------------
@@ -128,7 +159,7 @@ def ramp_fdk(pre: torch.Tensor, scan, bp: api.Backprojector, A) -> torch.Tensor:
     return bp.finalize()
 
 
-def train(steps: int = 150, batch: int = 8, T: int = 64, lr: float = 2e-3, seed0: int = 1000,
+def train(steps: int = 200, batch: int = 8, T: int = 64, lr: float = 1e-4, seed0: int = 1000,
           wl: Workload | None = None, log=None):
     """Train the taps through the GPU forward and backward kernels on batches
     of seeded phantoms (seeds seed0 + k).  Returns (module, losses)."""
@@ -137,7 +168,7 @@ def train(steps: int = 150, batch: int = 8, T: int = 64, lr: float = 2e-3, seed0
     A = api.carm_matrices(scan)
     data = PhantomData(wl, A)
     filt = LearnedRowFilter(T, tau=api.iso_pitch(scan)).cuda()
-    opt = torch.optim.Adam(filt.parameters(), lr=lr * float(filt.taps.detach().abs().max()))
+    opt = torch.optim.Adam(filt.parameters(), lr=lr)
     bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
     pool = [data.sample(seed0 + k) for k in range(batch * 4)]
     losses = []
@@ -149,7 +180,7 @@ def train(steps: int = 150, batch: int = 8, T: int = 64, lr: float = 2e-3, seed0
             volume = backproject(filt(pre), bp, A)
             loss = torch.mean((volume - target) ** 2) / batch
             loss.backward()
-            total += float(loss)
+            total += float(loss.detach())
         opt.step()
         losses.append(total)
         if log is not None and (it % 25 == 0 or it == steps - 1):
