@@ -74,8 +74,20 @@ typedef enum {
      * (the rest along z), or a two-digit code XY = X lanes along x by Y along
      * y (44, 42, 82, 24; the rest along z).  Default 8.  Changes speed only:
      * every voxel still sums its projections in the same order. */
-    BP_OPT_LANES_X = 4
+    BP_OPT_LANES_X = 4,
+    /* Data path of the backprojection: 0 (default) automatic, 1 texture
+     * gathers, 2 TMA-staged shared-memory tiles.  Both give identical
+     * volumes; the automatic choice takes the TMA path when the footprint of
+     * a 16 x 8 x 8 voxel brick fits its tile for every projection of the
+     * batch.  bp_query(BP_QUERY_LAST_PATH) reports the path taken. */
+    BP_OPT_PATH = 5
 } bp_option;
+
+/* Queries for bp_query. */
+typedef enum {
+    BP_QUERY_LAST_PATH = 1,          /* data path of the last batch: 1 texture, 2 TMA, 0 none yet */
+    BP_QUERY_PROJECTIONS_ADDED = 2   /* projections accumulated since create / reset / set_state */
+} bp_query_what;
 
 /* ---------------------------------------------------------------- context */
 
@@ -140,6 +152,9 @@ bp_status bp_set_state(bp_ctx *ctx, const float *vol_in, int on_device, long lon
  * between runs.  Leaves the context's volume untouched. */
 bp_status bp_adjoint(bp_ctx *ctx, const float *vol, int vol_on_device,
                      const double *A, int n, float *images_out, int out_on_device);
+
+/* Read a bp_query_what value into *value.  BP_EINVAL for an unknown query. */
+bp_status bp_query(const bp_ctx *ctx, int what, long long *value);
 
 /* Device time of the backprojection kernel launches recorded while
  * BP_OPT_TIMING was on (measurement support, in the spirit of the paper's

@@ -11,7 +11,8 @@ from . import build as _build
 
 BP_OK, BP_EINVAL, BP_ENOMEM, BP_ECUDA, BP_ESTATE, BP_ETIMEOUT = range(6)
 BP_F32, BP_F16, BP_BF16 = 0, 1, 2
-BP_OPT_IEEE_RCP, BP_OPT_BATCH, BP_OPT_TIMING, BP_OPT_LANES_X = 1, 2, 3, 4
+BP_OPT_IEEE_RCP, BP_OPT_BATCH, BP_OPT_TIMING, BP_OPT_LANES_X, BP_OPT_PATH = 1, 2, 3, 4, 5
+BP_QUERY_LAST_PATH, BP_QUERY_PROJECTIONS_ADDED = 1, 2
 STATUS_NAMES = {0: "BP_OK", 1: "BP_EINVAL", 2: "BP_ENOMEM", 3: "BP_ECUDA", 4: "BP_ESTATE", 5: "BP_ETIMEOUT"}
 
 # Every symbol include/bp1104.h declares, with (restype, argtypes).
@@ -27,6 +28,7 @@ SIGNATURES = {
     "bp_set_state": (_i, [_vp, _vp, _i, _ll]),
     "bp_adjoint": (_i, [_vp, _vp, _i, _vp, _i, _vp, _i]),
     "bp_kernel_stats": (_i, [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_d)]),
+    "bp_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "bp_probe_gather": (_i, [_i, ctypes.POINTER(_d)]),
     "bp_last_error": (ctypes.c_char_p, [_vp]),
     "bp_carm_matrices": (_i, [_i, _vp, _d, _d, _d, _d, _d, _vp, _vp]),
@@ -123,6 +125,12 @@ def bp_set_state(ctx, vol_ptr, on_device, n_added):
 def bp_adjoint(ctx, vol_ptr, vol_on_device, A_ptr, n, out_ptr, out_on_device):
     check(lib().bp_adjoint(ctx, vol_ptr, int(vol_on_device), A_ptr, int(n), out_ptr,
                            int(out_on_device)), ctx)
+
+
+def bp_query(ctx, what) -> int:
+    v = _ll(0)
+    check(lib().bp_query(ctx, int(what), ctypes.byref(v)), ctx)
+    return v.value
 
 
 def bp_kernel_stats(ctx):

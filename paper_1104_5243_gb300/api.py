@@ -84,6 +84,14 @@ class Backprojector:
     def reset(self):
         N.bp_reset(self._ctx)
 
+    def query(self, what: int) -> int:
+        return N.bp_query(self._ctx, what)
+
+    @property
+    def last_path(self) -> str:
+        """Data path of the last batch: 'texture', 'tma' or 'none'."""
+        return {0: "none", 1: "texture", 2: "tma"}[N.bp_query(self._ctx, N.BP_QUERY_LAST_PATH)]
+
     def kernel_stats(self):
         """(launches, total ms) of backprojection kernels timed since the
         last call (needs set_option(BP_OPT_TIMING, 1))."""

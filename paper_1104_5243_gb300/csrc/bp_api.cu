@@ -21,6 +21,28 @@ namespace bp {
 const char *thread_error();
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
+// query (no link against libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
 using namespace bp;
 
 struct bp_ctx {
@@ -47,6 +69,14 @@ struct bp_ctx {
     int next_set = 0;
     bool timing = false;
     std::vector<cudaEvent_t> ev;   // start/stop pairs, reused
+    int path = 0;                  // BP_OPT_PATH: 0 auto, 1 texture, 2 TMA
+    int last_path = 0;             // path of the last batch (1 or 2)
+    // TMA path: pair images per set (kMaxBatch slots each) and their maps
+    void *pairs[2] = {nullptr, nullptr};
+    size_t pair_pitch = 0;         // pair elements per row
+    size_t pair_slot_bytes = 0;
+    CUtensorMap maps[2][kMaxBatch];
+    int *err_dev = nullptr;        // set by a kernel whose bounded wait gave up
     size_t ev_used = 0;
     char err[1024] = "no error";
 };
@@ -89,6 +119,8 @@ static void release(bp_ctx *c)
         }
         if (c->staging[s])
             cudaFree(c->staging[s]);
+        if (c->pairs[s])
+            cudaFree(c->pairs[s]);
         if (c->copy_done[s])
             cudaEventDestroy(c->copy_done[s]);
         if (c->kern_done[s])
@@ -100,6 +132,8 @@ static void release(bp_ctx *c)
         cudaEventDestroy(e);
     if (c->vol)
         cudaFree(c->vol);
+    if (c->err_dev)
+        cudaFree(c->err_dev);
     if (c->copy_stream)
         cudaStreamDestroy(c->copy_stream);
 }
@@ -170,6 +204,9 @@ extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
     }
     const size_t nvox = (size_t)L * L * L;
     check(cudaMalloc((void **)&c->vol, nvox * sizeof(float)), "cudaMalloc(volume)");
+    check(cudaMalloc((void **)&c->err_dev, sizeof(int)), "cudaMalloc(error flag)");
+    if (st == BP_OK)
+        check(cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream), "cudaMemsetAsync");
     if (st == BP_OK)
         check(cudaMemsetAsync(c->vol, 0, nvox * sizeof(float), c->stream), "cudaMemsetAsync");
     for (int s = 0; s < 2 && st == BP_OK; ++s)
@@ -222,6 +259,11 @@ extern "C" bp_status bp_set_option(bp_ctx *c, int option, long long value)
         if (value != 8 && value != 16 && value != 32 && value != 44 && value != 42 && value != 82 && value != 24)
             return fail(c, BP_EINVAL, "bp_set_option: LANES_X takes 8, 16, 32, 44, 42, 82 or 24");
         c->lanes_x = (int)value;
+        return BP_OK;
+    case BP_OPT_PATH:
+        if (value < 0 || value > 2)
+            return fail(c, BP_EINVAL, "bp_set_option: PATH takes 0 (auto), 1 (texture) or 2 (TMA)");
+        c->path = (int)value;
         return BP_OK;
     case BP_OPT_TIMING:
         if (value != 0 && value != 1)
@@ -299,6 +341,110 @@ static VolGeom vol_geom(const bp_ctx *c)
     return g;
 }
 
+static int pair_kind(const bp_ctx *c)
+{
+    return c->dtype == BP_F32 ? kPairF32 : c->dtype == BP_F16 ? kPairF16 : kPairBF16;
+}
+
+// Pair images for the TMA path: allocated on first use, with one tensor map
+// per slot (the slots' addresses never change).
+static bp_status ensure_pairs(bp_ctx *c)
+{
+    if (c->pairs[0] != nullptr)
+        return BP_OK;
+    EncodeTiledFn enc = encode_tiled();
+    if (enc == nullptr)
+        return fail(c, BP_ECUDA, "TMA path: cuTensorMapEncodeTiled is not available from the driver");
+    const int kind = pair_kind(c);
+    const size_t pair_bytes = kind == kPairF32 ? 8 : 4;
+    const size_t align = kind == kPairF32 ? 2 : 4;               // pairs per 16 bytes
+    const size_t width = (size_t)c->isx + 1;                     // pair columns 0 .. isx
+    c->pair_pitch = (width + align - 1) / align * align;
+    c->pair_slot_bytes = c->pair_pitch * pair_bytes * c->isy;
+    const size_t words = pair_bytes / 4;
+    for (int s = 0; s < 2; ++s) {
+        CTX_CK(c, cudaMalloc(&c->pairs[s], c->pair_slot_bytes * kMaxBatch));
+        for (int j = 0; j < kMaxBatch; ++j) {
+            void *base = static_cast<char *>(c->pairs[s]) + c->pair_slot_bytes * j;
+            const cuuint64_t dims[2] = {width * words, (cuuint64_t)c->isy};
+            const cuuint64_t strides[1] = {c->pair_pitch * pair_bytes};
+            const cuuint32_t box[2] = {(cuuint32_t)((kind == kPairF32 ? TmaBox<kPairF32>::BU : TmaBox<kPairF16>::BU) * words),
+                                       (cuuint32_t)(kind == kPairF32 ? TmaBox<kPairF32>::BV : TmaBox<kPairF16>::BV)};
+            const cuuint32_t estr[2] = {1, 1};
+            CUresult r = enc(&c->maps[s][j], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail(c, BP_ECUDA, "TMA path: cuTensorMapEncodeTiled failed (%d)", (int)r);
+        }
+    }
+    return BP_OK;
+}
+
+// Host estimate for the automatic path choice: do at least half of the
+// footprints of the 8 bricks at the volume's corners (the most magnified
+// ones), over the batch's projections, fit the TMA box?  Then nearly all
+// bricks fit, and the few that do not take the kernel's global-memory path,
+// so this only picks the faster kernel, never a wrong one.
+static bool tma_fits(const bp_ctx *c, const double *A, int n)
+{
+    const int kind = pair_kind(c);
+    const int BU = kind == kPairF32 ? TmaBox<kPairF32>::BU : TmaBox<kPairF16>::BU;
+    const int BV = kind == kPairF32 ? TmaBox<kPairF32>::BV : TmaBox<kPairF16>::BV;
+    const int align = kind == kPairF32 ? 2 : 4;
+    const int L = c->L;
+    const int bl[3] = {kBrickX, kBrickY, kBrickZ};
+    long long fit = 0, total = 0;
+    for (int i = 0; i < n; ++i) {
+        const double *a = A + 12 * (size_t)i;
+        for (int corner = 0; corner < 8; ++corner) {
+            int lo[3], hi[3];
+            for (int d = 0; d < 3; ++d) {
+                const bool up = (corner >> d) & 1;
+                const int first = up ? (L - 1) / bl[d] * bl[d] : 0;
+                lo[d] = first;
+                hi[d] = std::min(first + bl[d], L) - 1;
+            }
+            double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+            for (int q = 0; q < 8; ++q) {
+                const double X = c->O[0] + c->R * ((q & 1) ? hi[0] : lo[0]);
+                const double Y = c->O[1] + c->R * ((q & 2) ? hi[1] : lo[1]);
+                const double Z = c->O[2] + c->R * ((q & 4) ? hi[2] : lo[2]);
+                const double w = a[8] * X + a[9] * Y + a[10] * Z + a[11];
+                const double u = (a[0] * X + a[1] * Y + a[2] * Z + a[3]) / w;
+                const double v = (a[4] * X + a[5] * Y + a[6] * Z + a[7]) / w;
+                umin = std::min(umin, u);
+                umax = std::max(umax, u);
+                vmin = std::min(vmin, v);
+                vmax = std::max(vmax, v);
+            }
+            // the kernel's margins (one pixel each side), alignment slack, and
+            // one more pixel for float32 rounding
+            ++total;
+            if (std::floor(umax) - std::floor(umin) + 3 + (align - 1) + 1 <= BU - 1 &&
+                std::floor(vmax) - std::floor(vmin) + 4 + 1 <= BV - 1)
+                ++fit;
+        }
+    }
+    return 2 * fit >= total;
+}
+
+static bp_status record_start(bp_ctx *c, cudaEvent_t *stop)
+{
+    *stop = nullptr;
+    if (!c->timing)
+        return BP_OK;
+    while (c->ev.size() < c->ev_used + 2) {
+        cudaEvent_t e;
+        CTX_CK(c, cudaEventCreate(&e));
+        c->ev.push_back(e);
+    }
+    CTX_CK(c, cudaEventRecord(c->ev[c->ev_used], c->stream));
+    *stop = c->ev[c->ev_used + 1];
+    c->ev_used += 2;
+    return BP_OK;
+}
+
 extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int images_on_device,
                                         const double *A, int n)
 {
@@ -316,7 +462,6 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
     CTX_CK(c, cudaSetDevice(c->device));
     const size_t img_elems = (size_t)c->isx * c->isy;
     const size_t row_bytes = sizeof(float) * c->isx;
-    const cudaMemcpyKind kind = images_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     // Work queued on the caller's stream before this call (e.g. the producer
     // of device images) must finish before the copy stream reads.
     CTX_CK(c, cudaEventRecord(c->inputs_ready, c->stream));
@@ -324,15 +469,22 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
     const VolGeom g = vol_geom(c);
     for (int c0 = 0; c0 < n; c0 += c->batch) {
         const int m = n - c0 < c->batch ? n - c0 : c->batch;
+        const double *A0 = A + 12 * (size_t)c0;
+        const bool tma = c->path == 2 || (c->path == 0 && tma_fits(c, A0, m));
+        if (tma) {
+            st = ensure_pairs(c);
+            if (st != BP_OK)
+                return st;
+        }
         const int s = c->next_set;
         c->next_set ^= 1;
         CTX_CK(c, cudaStreamWaitEvent(c->copy_stream, c->kern_done[s], 0));
         const float *src0 = images + (size_t)c0 * img_elems;
-        if (c->dtype == BP_F32 && !images_on_device) {
+        if (!tma && c->dtype == BP_F32 && !images_on_device) {
             // host images go straight into the arrays on the copy engine
             for (int j = 0; j < m; ++j)
                 CTX_CK(c, cudaMemcpy2DToArrayAsync(c->arr[s][j], 0, 0, src0 + (size_t)j * img_elems, row_bytes,
-                                                   row_bytes, c->isy, kind, c->copy_stream));
+                                                   row_bytes, c->isy, cudaMemcpyHostToDevice, c->copy_stream));
         } else {
             const float *src = src0;
             if (!images_on_device) {
@@ -342,50 +494,104 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                                           cudaMemcpyHostToDevice, c->copy_stream));
                 src = c->staging[s];
             }
-            ConvBatch cb;
-            cb.n = m;
-            for (int j = 0; j < m; ++j) {
-                cb.src[j] = src + (size_t)j * img_elems;
-                cb.surf[j] = c->surf[s][j];
+            if (tma) {
+                PairBatch pb;
+                pb.n = m;
+                for (int j = 0; j < m; ++j) {
+                    pb.src[j] = src + (size_t)j * img_elems;
+                    pb.dst[j] = static_cast<char *>(c->pairs[s]) + c->pair_slot_bytes * j;
+                }
+                CTX_CK(c, launch_pair_images(pb, c->isx, c->isy, (int)c->pair_pitch, pair_kind(c), c->copy_stream));
+            } else {
+                ConvBatch cb;
+                cb.n = m;
+                for (int j = 0; j < m; ++j) {
+                    cb.src[j] = src + (size_t)j * img_elems;
+                    cb.surf[j] = c->surf[s][j];
+                }
+                const int mode = c->dtype == BP_F32 ? 0 : c->dtype == BP_F16 ? 1 : 2;
+                CTX_CK(c, launch_convert(cb, c->isx, c->isy, mode, c->copy_stream));
             }
-            const int mode = c->dtype == BP_F32 ? 0 : c->dtype == BP_F16 ? 1 : 2;
-            CTX_CK(c, launch_convert(cb, c->isx, c->isy, mode, c->copy_stream));
         }
         CTX_CK(c, cudaEventRecord(c->copy_done[s], c->copy_stream));
         CTX_CK(c, cudaStreamWaitEvent(c->stream, c->copy_done[s], 0));
-        FwdBatch b;
-        b.n = m;
-        for (int j = 0; j < m; ++j) {
-            const double *a = A + 12 * (size_t)(c0 + j);
-            // u' = u - ku + 1 = (uw - (ku - 1) w) / w; gather at floor(u') + ku
-            double ku, kv;
-            centre_offsets(c, a, &ku, &kv);
-            b.m[j][0] = row4(a, 0, 1.0 - ku);
-            b.m[j][1] = row4(a, 1, 1.0 - kv);
-            b.m[j][2] = row4(a, 2, 0.0);
-            b.k[j] = make_float2((float)ku, (float)kv);
-            b.tex[j] = c->tex[s][j];
-        }
-        cudaEvent_t ev_stop = nullptr;
-        if (c->timing) {
-            while (c->ev.size() < c->ev_used + 2) {
-                cudaEvent_t e;
-                CTX_CK(c, cudaEventCreate(&e));
-                c->ev.push_back(e);
+        cudaEvent_t ev_stop;
+        st = record_start(c, &ev_stop);
+        if (st != BP_OK)
+            return st;
+        if (tma) {
+            TmaBatch tb;   // 12 KB of kernel parameters
+            tb.n = m;
+            tb.isx = c->isx;
+            tb.isy = c->isy;
+            tb.pitch = (int)c->pair_pitch;
+            for (int j = 0; j < m; ++j) {
+                const double *a = A0 + 12 * (size_t)j;
+                double ku, kv;
+                centre_offsets(c, a, &ku, &kv);
+                tb.m[j][0] = row4(a, 0, 1.0 - ku);
+                tb.m[j][1] = row4(a, 1, 1.0 - kv);
+                tb.m[j][2] = row4(a, 2, 0.0);
+                tb.k[j] = make_int2((int)ku, (int)kv);
+                tb.map[j] = c->maps[s][j];
+                tb.img[j] = static_cast<const char *>(c->pairs[s]) + c->pair_slot_bytes * j;
             }
-            CTX_CK(c, cudaEventRecord(c->ev[c->ev_used], c->stream));
-            ev_stop = c->ev[c->ev_used + 1];
-            c->ev_used += 2;
+            CTX_CK(c, launch_bp_tma(tb, c->vol, g, pair_kind(c), !c->vol_zero, c->ieee_rcp, c->err_dev, c->stream));
+        } else {
+            FwdBatch b;
+            b.n = m;
+            for (int j = 0; j < m; ++j) {
+                const double *a = A0 + 12 * (size_t)j;
+                // u' = u - ku + 1 = (uw - (ku - 1) w) / w; gather at floor(u') + ku
+                double ku, kv;
+                centre_offsets(c, a, &ku, &kv);
+                b.m[j][0] = row4(a, 0, 1.0 - ku);
+                b.m[j][1] = row4(a, 1, 1.0 - kv);
+                b.m[j][2] = row4(a, 2, 0.0);
+                b.k[j] = make_float2((float)ku, (float)kv);
+                b.tex[j] = c->tex[s][j];
+            }
+            CTX_CK(c, launch_bp_fwd(b, c->vol, g, c->dtype == BP_BF16 ? kTexBF16 : kTexFloat, !c->vol_zero,
+                                    c->ieee_rcp, c->lanes_x, c->stream));
         }
-        CTX_CK(c, launch_bp_fwd(b, c->vol, g, c->dtype == BP_BF16 ? kTexBF16 : kTexFloat, !c->vol_zero,
-                                c->ieee_rcp, c->lanes_x, c->stream));
         if (ev_stop)
             CTX_CK(c, cudaEventRecord(ev_stop, c->stream));
+        c->last_path = tma ? 2 : 1;
         c->vol_zero = false;
         CTX_CK(c, cudaEventRecord(c->kern_done[s], c->stream));
     }
     c->n_added += n;
     return BP_OK;
+}
+
+// Turn the device-side error flag (a bounded wait that gave up) into a
+// status; clears the flag.  The caller has synchronised the stream.
+static bp_status check_device_error(bp_ctx *c, const char *who)
+{
+    int flag = 0;
+    CTX_CK(c, cudaMemcpy(&flag, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CTX_CK(c, cudaMemset(c->err_dev, 0, sizeof(int)));
+        return fail(c, BP_ETIMEOUT, "%s: a backprojection block gave up waiting for its projection tile; "
+                                    "the volume is incomplete", who);
+    }
+    return BP_OK;
+}
+
+extern "C" bp_status bp_query(const bp_ctx *c, int what, long long *value)
+{
+    if (c == nullptr || value == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_query: NULL argument");
+    switch (what) {
+    case BP_QUERY_LAST_PATH:
+        *value = c->last_path;
+        return BP_OK;
+    case BP_QUERY_PROJECTIONS_ADDED:
+        *value = c->n_added;
+        return BP_OK;
+    default:
+        return fail(nullptr, BP_EINVAL, "bp_query: unknown query %d", what);
+    }
 }
 
 extern "C" bp_status bp_kernel_stats(bp_ctx *c, long long *launches, double *total_ms)
@@ -394,6 +600,9 @@ extern "C" bp_status bp_kernel_stats(bp_ctx *c, long long *launches, double *tot
         return fail(nullptr, BP_EINVAL, "bp_kernel_stats: NULL context");
     CTX_CK(c, cudaSetDevice(c->device));
     CTX_CK(c, cudaStreamSynchronize(c->stream));
+    bp_status st = check_device_error(c, "bp_kernel_stats");
+    if (st != BP_OK)
+        return st;
     double ms = 0.0;
     for (size_t q = 0; q + 1 < c->ev_used; q += 2) {
         float t = 0.f;
@@ -419,7 +628,7 @@ extern "C" bp_status bp_finalize(bp_ctx *c, float *vol_out, int on_device)
     CTX_CK(c, cudaMemcpyAsync(vol_out, c->vol, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                               c->stream));
     CTX_CK(c, cudaStreamSynchronize(c->stream));
-    return BP_OK;
+    return check_device_error(c, "bp_finalize");
 }
 
 extern "C" bp_status bp_get_state(bp_ctx *c, float *vol_out, int on_device, long long *n_added)

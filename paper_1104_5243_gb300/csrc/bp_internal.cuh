@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (that is include/bp1104.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -58,6 +59,45 @@ cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int t
 
 cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom &g,
                               float *out, int isx, int isy, bool ieee_rcp, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// TMA / shared-memory path (bp_tma.cu).  Bricks of 16 x 8 x 8 voxels per
+// 256-thread block; projections staged as "pair images" (element c of a row
+// holds pixels c-1 and c) and loaded per brick and projection as one TMA box
+// of BU pair columns by BV rows.
+constexpr int kBrickX = 16, kBrickY = 8, kBrickZ = 8;
+enum PairKind { kPairF32 = 0, kPairF16 = 1, kPairBF16 = 2 };
+template <int KIND> struct TmaBox;
+// Row pitches of 528 B (f32 pairs) and 272 B (16-bit pairs) put successive
+// box rows 4 banks apart, so lanes on the same column in different rows do
+// not conflict.
+template <> struct TmaBox<kPairF32> { static constexpr int BU = 66, BV = 32; };
+template <> struct TmaBox<kPairF16> { static constexpr int BU = 68, BV = 32; };
+template <> struct TmaBox<kPairBF16> { static constexpr int BU = 68, BV = 32; };
+// 32-bit words per pair, and the pair-column alignment that keeps the TMA
+// box origin on a 16-byte boundary.
+template <int KIND> constexpr int kPairWords = KIND == kPairF32 ? 2 : 1;
+template <int KIND> constexpr int kPairAlign = KIND == kPairF32 ? 2 : 4;
+constexpr int kTmaWaitIters = 1 << 22;
+constexpr int kTmaStages = 3;   // depth of the shared-memory ring
+
+struct TmaBatch {
+    CUtensorMap map[kMaxBatch];        // one per projection's pair image
+    float4 m[kMaxBatch][3];            // rows as in FwdBatch (centred, +1 folded)
+    int2 k[kMaxBatch];                 // integer centring offsets (ku, kv)
+    const void *img[kMaxBatch];        // pair image base, for the global path
+    int n, isx, isy, pitch;            // pitch: pair elements per row
+};
+
+cudaError_t launch_bp_tma(const TmaBatch &b, float *vol, const VolGeom &g, int pair_kind, bool accumulate,
+                          bool ieee_rcp, int *err, cudaStream_t s);
+
+struct PairBatch {
+    const float *src[kMaxBatch];
+    void *dst[kMaxBatch];
+    int n;
+};
+cudaError_t launch_pair_images(const PairBatch &b, int isx, int isy, int pitch, int pair_kind, cudaStream_t s);
 
 // Copy (mode 0) or FP16 (1) / BF16 (2) conversion of up to kMaxBatch FP32
 // images into the projection arrays' surfaces.

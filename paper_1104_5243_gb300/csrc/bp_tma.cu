@@ -1,0 +1,418 @@
+// Backprojection with projections staged through TMA into shared memory
+// (Sect. 3.1, Listing 1; the same arithmetic as bp_fwd.cu, different data
+// path).
+//
+// Why: the texture unit returns 2x2 gathers of 32-bit texels at half the
+// rate of 16-bit ones, which bounds the float32 form of the texture kernel.
+// Here each block owns a 16 x 8 x 8 voxel brick; for every projection a
+// producer warp projects the brick's 8 corners (one lane each), and either
+//   * culls the projection when the footprint misses the detector (every
+//     term is then exactly zero -- the line-wise clipping of Sect. 3.3 at
+//     brick granularity), or
+//   * issues one cp.async.bulk.tensor.2d load of the footprint box from the
+//     projection's "pair image" into a stage of a shared-memory ring,
+//     completing on an mbarrier; out-of-range rows/columns are zero-filled
+//     by the TMA unit, which is the zero padding of Sect. 3.3, or
+//   * (footprint larger than the box) marks the projection for the
+//     bounds-checked global-memory path.
+// The pair image stores element c = (p[c-1], p[c]) of each row (zero outside
+// the detector), so the four corners of an update are two shared-memory
+// loads: (tl, tr) from row iv and (bl, br) from row iv+1.
+//
+// The coordinates, fractions and interpolation are computed exactly as in
+// the texture kernel, so both paths give bit-identical volumes.
+//
+// Every wait on an mbarrier is bounded; on timeout the block records an
+// error flag the host turns into BP_ETIMEOUT, the producer waits (bounded)
+// for the copies it has in flight, and the block returns.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "bp_internal.cuh"
+
+namespace bp {
+
+template <bool IEEE>
+__device__ __forceinline__ float recip_tma(float w)
+{
+    if constexpr (IEEE) {
+        return __frcp_rn(w);
+    } else {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(w));
+        return r;
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: about a second at most (try_wait itself suspends briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (int it = 0; it < kTmaWaitIters; ++it)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Integer value of an integer-valued float with |f| < 2^22, without the
+// float-to-int conversion unit: adding 1.5 * 2^23 puts the integer in the
+// low mantissa bits.
+__device__ __forceinline__ int int_of_integral(float f)
+{
+    return __float_as_int(f + 12582912.0f) - 0x4B400000;
+}
+
+// The four corners of an update from two pair loads.  Pair = (left, right).
+template <int KIND>
+struct Pairs;
+
+template <>
+struct Pairs<kPairF32> {
+    using T = float2;
+    __device__ static float2 unpack(float2 p) { return p; }
+};
+
+template <>
+struct Pairs<kPairF16> {
+    using T = unsigned int;
+    __device__ static float2 unpack(unsigned int p)
+    {
+        return __half22float2(*reinterpret_cast<const __half2 *>(&p));
+    }
+};
+
+template <>
+struct Pairs<kPairBF16> {
+    using T = unsigned int;
+    __device__ static float2 unpack(unsigned int p)
+    {
+        return make_float2(__uint_as_float(p << 16), __uint_as_float(p & 0xffff0000u));
+    }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised pipeline: warps 0..7 compute (256 consumer threads, 4
+// voxels each), warp 8 is the producer.  Stage s of the kTmaStages-deep ring
+// has a "full" barrier (the producer's arrival, plus the TMA bytes when a
+// tile is loaded) and an "empty" barrier (one arrival per consumer warp when
+// it is done with the stage).  No block-wide barrier inside the loop.
+template <int KIND, bool IEEE>
+__global__ void __launch_bounds__(kThreads + 32, 4)
+bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const VolGeom g, int accumulate,
+              int *__restrict__ err)
+{
+    using P = Pairs<KIND>;
+    using T = typename P::T;
+    constexpr int BU = TmaBox<KIND>::BU, BV = TmaBox<KIND>::BV;
+    constexpr int kBufElems = BU * BV;
+    constexpr int S = kTmaStages;
+    constexpr int kConsumerWarps = kThreads / 32;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];   // the ring: S stages of kBufElems pairs
+    T (*buf)[kBufElems] = reinterpret_cast<T (*)[kBufElems]>(dyn_smem);
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    // per stage: mode (0 culled, 1 shared memory, 2 global) and box origin
+    __shared__ int meta_mode[S], meta_cx0[S], meta_ry0[S];
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = g.L;
+    const int bx0 = blockIdx.x * kBrickX, by0 = blockIdx.y * kBrickY, bz0 = blockIdx.z * kBrickZ;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kConsumerWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps) {
+        // ---------------- producer: classify each projection, start copies
+        const int xe = min(bx0 + kBrickX, L) - 1, ye = min(by0 + kBrickY, L) - 1, ze = min(bz0 + kBrickZ, L) - 1;
+        const int c = lane & 7;   // lanes 0..7 take one brick corner each
+        const float X = fmaf(g.R, (float)((c & 1) ? xe : bx0), g.Ox);
+        const float Yc = fmaf(g.R, (float)((c & 2) ? ye : by0), g.Oy);
+        const float Z = fmaf(g.R, (float)((c & 4) ? ze : bz0), g.Oz);
+        int issued = 0;            // stages whose tile may still be in flight
+        int last_use[S] = {};      // use index of each stage's last tile
+        for (int i = 0; i < b.n; ++i) {
+            const int st = i % S, use = i / S;
+            if (use > 0 && !mbar_wait_bounded(&empty[st], (use - 1) & 1)) {
+                if (lane == 0) {
+                    atomicExch(&abort_flag, 1);
+                    atomicExch(err, 1);
+                }
+                break;
+            }
+            if (*(volatile int *)&abort_flag)
+                break;
+            const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+            const float w = fmaf(rw.x, X, fmaf(rw.y, Yc, fmaf(rw.z, Z, rw.w)));
+            const float r = 1.0f / w;
+            const float u = fmaf(ru.x, X, fmaf(ru.y, Yc, fmaf(ru.z, Z, ru.w))) * r;
+            const float v = fmaf(rv.x, X, fmaf(rv.y, Yc, fmaf(rv.z, Z, rv.w))) * r;
+            float umin = u, umax = u, vmin = v, vmax = v;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+                umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+                vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+                vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            }
+            if (lane == 0) {
+                const int2 kc = b.k[i];
+                umin = fminf(fmaxf(umin, -1.0e6f), 1.0e6f);   // keep the int conversions in range
+                umax = fminf(fmaxf(umax, -1.0e6f), 1.0e6f);
+                vmin = fminf(fmaxf(vmin, -1.0e6f), 1.0e6f);
+                vmax = fminf(fmaxf(vmax, -1.0e6f), 1.0e6f);
+                // pair columns and image rows touched, one pixel of margin
+                // (pair column = floor(u') + ku; top row = floor(v') + kv - 1)
+                const int cmin = (int)floorf(umin) + kc.x - 1, cmax = (int)floorf(umax) + kc.x + 1;
+                const int rmin = (int)floorf(vmin) + kc.y - 2, rmax = (int)floorf(vmax) + kc.y + 1;
+                int mode, cx0 = 0, ry0 = 0;
+                if (cmax < 0 || cmin > b.isx || rmax < 0 || rmin > b.isy - 1) {
+                    mode = 0;   // nothing of this brick lands on the detector
+                } else {
+                    cx0 = cmin & ~(kPairAlign<KIND> - 1);
+                    ry0 = rmin;
+                    mode = (cmax < cx0 + BU && rmax < ry0 + BV) ? 1 : 2;
+                }
+                meta_mode[st] = mode;
+                meta_cx0[st] = cx0;
+                meta_ry0[st] = ry0;
+                if (mode == 1) {
+                    mbar_expect_tx(&full[st], (uint32_t)(kBufElems * sizeof(T)));   // also publishes meta
+                    tma_load_2d(buf[st], &b.map[i], cx0 * kPairWords<KIND>, ry0, &full[st]);
+                    issued |= 1 << st;
+                    last_use[st] = use;
+                } else {
+                    mbar_arrive(&full[st]);
+                    issued &= ~(1 << st);
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0 && *(volatile int *)&abort_flag) {
+            // let copies still in flight land before the block's memory goes away
+            for (int q = 0; q < S; ++q)
+                if (issued & (1 << q))
+                    mbar_wait_bounded(&full[q], last_use[q] & 1);
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    const int tx = lane & 7, tz = lane >> 3;
+    // this lane's voxels: x0 + {0, 8}, y, z0 + {0, 4}
+    const int x0 = bx0 + tx, y = by0 + warp, z0 = bz0 + tz;
+    const float Xv[2] = {fmaf(g.R, (float)x0, g.Ox), fmaf(g.R, (float)(x0 + 8), g.Ox)};
+    const float Y = fmaf(g.R, (float)y, g.Oy);
+    const float Zv[2] = {fmaf(g.R, (float)z0, g.Oz), fmaf(g.R, (float)(z0 + 4), g.Oz)};
+
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    bool ok = true;
+#pragma unroll 1
+    for (int i = 0; i < b.n; ++i) {
+        const int s = i % S;
+        if (!mbar_wait_bounded(&full[s], (i / S) & 1)) {
+            if (lane == 0) {
+                atomicExch(&abort_flag, 1);
+                atomicExch(err, 1);
+            }
+            ok = false;
+            break;
+        }
+        const int mode = meta_mode[s];
+        if (mode != 0) {
+            const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+            const int2 kc = b.k[i];
+            // column / row offsets that turn floor(u'), floor(v') into
+            // indices of the staged box (or of the global pair image)
+            const int cu = kc.x - (mode == 1 ? meta_cx0[s] : 0);
+            const int cv = kc.y - 1 - (mode == 1 ? meta_ry0[s] : 0);
+#pragma unroll
+            for (int kz = 0; kz < 2; ++kz) {
+                const float bu = fmaf(ru.y, Y, fmaf(ru.z, Zv[kz], ru.w));
+                const float bv = fmaf(rv.y, Y, fmaf(rv.z, Zv[kz], rv.w));
+                const float bw = fmaf(rw.y, Y, fmaf(rw.z, Zv[kz], rw.w));
+#pragma unroll
+                for (int kx = 0; kx < 2; ++kx) {
+                    const float uw = fmaf(ru.x, Xv[kx], bu);
+                    const float vw = fmaf(rv.x, Xv[kx], bv);
+                    const float w = fmaf(rw.x, Xv[kx], bw);
+                    const float r = recip_tma<IEEE>(w);
+                    const float u = uw * r, v = vw * r;
+                    const float fu0 = floorf(u), fv0 = floorf(v);
+                    const int col = int_of_integral(fu0) + cu;
+                    const int row = int_of_integral(fv0) + cv;
+                    float2 top, bot;
+                    if (mode == 1) {
+                        // the corner-based box covers every voxel of the
+                        // volume with a pixel of margin; the clamp only
+                        // guards the array for lanes beyond a ragged edge
+                        const int idx = min(max(row * BU + col, 0), kBufElems - BU - 1);
+                        const T *p = buf[s] + idx;
+                        top = P::unpack(p[0]);
+                        bot = P::unpack(p[BU]);
+                    } else {
+                        // footprint larger than the box: read the pair image
+                        // directly, rows outside the detector are zero
+                        const T *img = reinterpret_cast<const T *>(b.img[i]);
+                        const bool cok = col >= 0 && col <= b.isx;
+                        const T *p = img + (long long)row * b.pitch + col;
+                        const T zero{};
+                        top = P::unpack(cok && row >= 0 && row < b.isy ? p[0] : zero);
+                        bot = P::unpack(cok && row + 1 >= 0 && row + 1 < b.isy ? p[b.pitch] : zero);
+                    }
+                    const float fu = u - fu0, fv = v - fv0;
+                    const float t = fmaf(fu, top.y - top.x, top.x);
+                    const float bt = fmaf(fu, bot.y - bot.x, bot.x);
+                    const float fx = fmaf(fv, bt - t, t);
+                    acc[kz * 2 + kx] = fmaf(fx, r * r, acc[kz * 2 + kx]);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(&empty[s]);   // this warp is done with stage s
+    }
+
+    if (!ok || y >= L)
+        return;
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz) {
+        const int z = z0 + 4 * kz;
+        if (z >= L)
+            continue;
+        float *row = vol + ((size_t)z * L + y) * L;
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx) {
+            const int x = x0 + 8 * kx;
+            if (x < L)
+                row[x] = (accumulate ? row[x] : 0.f) + acc[kz * 2 + kx];
+        }
+    }
+}
+
+template <int KIND, bool IEEE>
+static cudaError_t launch_tma_kind(const TmaBatch &b, float *vol, const VolGeom &g, bool acc, int *err,
+                                   cudaStream_t s)
+{
+    dim3 grid((g.L + kBrickX - 1) / kBrickX, (g.L + kBrickY - 1) / kBrickY, (g.L + kBrickZ - 1) / kBrickZ);
+    using T = typename Pairs<KIND>::T;
+    const size_t smem = sizeof(T) * TmaBox<KIND>::BU * TmaBox<KIND>::BV * kTmaStages;
+    // the ring exceeds the 48 KB default for float32 pairs (set per call:
+    // cheap, and correct on whichever device is current)
+    cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<KIND, IEEE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    bp_tma_kernel<KIND, IEEE><<<grid, kThreads + 32, smem, s>>>(b, vol, g, acc ? 1 : 0, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bp_tma(const TmaBatch &b, float *vol, const VolGeom &g, int pair_kind, bool accumulate,
+                          bool ieee_rcp, int *err, cudaStream_t s)
+{
+    if (b.n <= 0)
+        return cudaSuccess;
+    switch (pair_kind) {
+    case kPairF32:
+        return ieee_rcp ? launch_tma_kind<kPairF32, true>(b, vol, g, accumulate, err, s)
+                        : launch_tma_kind<kPairF32, false>(b, vol, g, accumulate, err, s);
+    case kPairF16:
+        return ieee_rcp ? launch_tma_kind<kPairF16, true>(b, vol, g, accumulate, err, s)
+                        : launch_tma_kind<kPairF16, false>(b, vol, g, accumulate, err, s);
+    default:
+        return ieee_rcp ? launch_tma_kind<kPairBF16, true>(b, vol, g, accumulate, err, s)
+                        : launch_tma_kind<kPairBF16, false>(b, vol, g, accumulate, err, s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair images: element c of row k holds (p[k][c-1], p[k][c]) for
+// c = 0 .. isx (zero outside the detector), in the storage type; elements
+// c > isx of the padded row are zero.  One thread per element.
+template <int KIND>
+__global__ void __launch_bounds__(256)
+pair_image_kernel(const __grid_constant__ PairBatch b, int isx, int isy, int pitch)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    const int i = blockIdx.z;
+    if (c >= pitch || i >= b.n)
+        return;
+    const float *src = b.src[i] + (size_t)k * isx;
+    const float l = (c >= 1 && c <= isx) ? src[c - 1] : 0.f;
+    const float r = (c < isx) ? src[c] : 0.f;
+    const size_t o = (size_t)k * pitch + c;
+    if constexpr (KIND == kPairF32) {
+        reinterpret_cast<float2 *>(b.dst[i])[o] = make_float2(l, r);
+    } else if constexpr (KIND == kPairF16) {
+        const __half2 h = __floats2half2_rn(l, r);
+        reinterpret_cast<__half2 *>(b.dst[i])[o] = h;
+    } else {
+        const unsigned int lo = __bfloat16_as_ushort(__float2bfloat16_rn(l));
+        const unsigned int hi = __bfloat16_as_ushort(__float2bfloat16_rn(r));
+        reinterpret_cast<unsigned int *>(b.dst[i])[o] = lo | (hi << 16);
+    }
+}
+
+cudaError_t launch_pair_images(const PairBatch &b, int isx, int isy, int pitch, int pair_kind, cudaStream_t s)
+{
+    if (b.n <= 0)
+        return cudaSuccess;
+    dim3 grid((pitch + 255) / 256, isy, b.n);
+    if (pair_kind == kPairF32)
+        pair_image_kernel<kPairF32><<<grid, 256, 0, s>>>(b, isx, isy, pitch);
+    else if (pair_kind == kPairF16)
+        pair_image_kernel<kPairF16><<<grid, 256, 0, s>>>(b, isx, isy, pitch);
+    else
+        pair_image_kernel<kPairBF16><<<grid, 256, 0, s>>>(b, isx, isy, pitch);
+    return cudaGetLastError();
+}
+
+}  // namespace bp

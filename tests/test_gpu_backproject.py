@@ -180,3 +180,67 @@ def test_full_size_sampled_voxels(L, dtype, tol):
     print(f"{L}^3 {dtype} sampled rel-L2 {err:.3e} max-rel {np.max(np.abs(g - ref) / np.maximum(np.abs(ref), 1e-30)):.3e}")
     assert err <= tol
     bp.close()
+
+
+# ---------------------------------------------------------------------------
+# TMA / shared-memory data path: same arithmetic as the texture path, so the
+# volumes must agree bit for bit (culled bricks only skip exact zeros).
+def run_path(vol, scan, A, q, path, dtype="f32"):
+    api = native()
+    from paper_1104_5243_gb300 import _native as N
+    bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype)
+    bp.set_option(N.BP_OPT_PATH, path)
+    bp.add_projections(torch.from_numpy(np.ascontiguousarray(q)).cuda(), A)
+    out = bp.finalize().cpu()
+    taken = bp.last_path
+    bp.close()
+    return out, taken
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_tma_path_is_bit_identical_to_texture_path(dtype):
+    scan, vol, A, ell, q, ref = tiny_phantom_case()
+    tex, p1 = run_path(vol, scan, A, q, 1, dtype)
+    tma, p2 = run_path(vol, scan, A, q, 2, dtype)
+    assert (p1, p2) == ("texture", "tma")
+    assert torch.equal(tex, tma)
+    tol = {"f32": FP32_TOL, "f16": FP16_TOL, "bf16": BF16_TOL}[dtype]
+    assert rel_l2(tma.numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("L,isx,isy,n", [(37, 53, 41, 70), (1, 7, 5, 3), (40, 24, 10, 20)])
+def test_tma_path_ragged_and_partial_detector(L, isx, isy, n):
+    scan = synth.Scan(n=n, isx=isx, isy=isy, pitch=384.0 / isx if isx > 24 else 4.0)
+    vol = synth.Volume(L)
+    A = oracle.carm_matrices(scan)
+    q = np.random.default_rng(L + n).standard_normal((n, isy, isx)).astype(np.float32)
+    ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
+    tex, _ = run_path(vol, scan, A, q, 1)
+    tma, _ = run_path(vol, scan, A, q, 2)
+    assert torch.equal(tex, tma)
+    assert rel_l2(tma.numpy(), ref) <= FP32_TOL
+
+
+def test_tma_global_fallback_when_footprints_exceed_the_tile():
+    """256^3 with the full detector: most brick footprints are larger than the
+    shared-memory tile, so the forced TMA path reads the pair images from
+    global memory; still bit-identical to the texture path."""
+    scan = synth.Scan(n=40, isx=1248, isy=960, pitch=0.308)
+    vol = synth.Volume(256)
+    A = oracle.carm_matrices(scan)
+    q = synth.uniform_stack(scan.n, scan.isy, scan.isx, seed=11)
+    tex, _ = run_path(vol, scan, A, q, 1)
+    tma, _ = run_path(vol, scan, A, q, 2)
+    assert torch.equal(tex, tma)
+    idx = np.random.default_rng(1).integers(0, 256 ** 3, size=512)
+    ref = oracle.backproject_voxels(vol.L, vol.R, vol.O, q, A, idx)
+    assert rel_l2(tma.view(-1).numpy()[idx], ref) <= FP32_TOL
+
+
+def test_automatic_path_choice():
+    scan = synth.SCANS["full"]
+    A = oracle.carm_matrices(scan)[:8]
+    q = synth.uniform_stack(8, scan.isy, scan.isx, seed=3)
+    _, p512 = run_path(synth.Volume(512), scan, A, q, 0)
+    _, p256 = run_path(synth.Volume(256), scan, A, q, 0)
+    assert (p512, p256) == ("tma", "texture")
