@@ -214,6 +214,7 @@ def main():
     ap.add_argument("--ref-proj", type=int, default=48, help="projections per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint and learned-filter timings")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -268,6 +269,7 @@ def main():
                    for f in args.forms.split(",")}
     forms = {}
     kernel = {}
+    path_taken = {}
     clocks = None
     for form in args.forms.split(","):
         bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=form)
@@ -292,6 +294,7 @@ def main():
             torch.cuda.synchronize()
         ms = max_over_ranks(t0.elapsed_time(t1))
         launches, kms = bp.kernel_stats()
+        path_taken[form] = bp.last_path
         bp.set_option(N.BP_OPT_TIMING, 0)
         gups = updates * args.steps * world / (ms / 1e3) / 1e9
         forms[form] = {"value": round(gups, 2), "ms_per_step": round(ms / args.steps, 3)}
@@ -325,6 +328,44 @@ def main():
         e2e = {"value": round(updates * args.steps * world / wall / 1e9, 2), "unit": UNIT,
                "h2d_bytes_per_step": int(stack_host.numel() * 4),
                "d2h_bytes_per_step": int(vol_host.numel() * 4)}
+
+    # The other two timed paths of the method: the adjoint (B^T, the autograd
+    # backward) on the differentiation workload, 256^3 -> 248 x 624x480, and
+    # one training step of the learned filter (8 phantoms at 128^3 x 120 x
+    # 312x240: row filter, backprojection, adjoint, filter gradient).
+    extra = {}
+    if not args.no_extra:
+        half = synth.SCANS["half"]
+        vh = synth.Volume(256)
+        Ah = api.carm_matrices(half)
+        fvol = torch.from_numpy(synth.uniform_volume(256, seed=5)).cuda()
+        gproj = torch.empty((half.n, half.isy, half.isx), dtype=torch.float32, device="cuda")
+        bp = api.Backprojector(vh.L, vh.R, vh.O, half.isx, half.isy)
+        for _ in range(args.warmup):
+            bp.adjoint(fvol, Ah, out=gproj)
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            bp.adjoint(fvol, Ah, out=gproj)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ams = t0.elapsed_time(t1) / args.steps
+        bp.close()
+        extra["adjoint"] = {"workload": "B^T 256^3 -> 248 x 624x480", "ms_per_call": round(ams, 3),
+                            "gups": round(256 ** 3 * half.n / (ams / 1e3) / 1e9, 2)}
+        from paper_1104_5243_gb300 import learned as lm
+        torch.manual_seed(0)
+        lm.train(steps=args.warmup, batch=8)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        lm.train(steps=args.steps, batch=8)
+        torch.cuda.synchronize()
+        extra["learned_filter_train_step"] = {
+            "workload": "8 phantoms, 128^3 x 120 x 312x240, forward + backward + Adam",
+            "ms_per_step": round((time.perf_counter() - t) / args.steps * 1e3, 2),
+            "note": "includes generating the phantom batch on the GPU once per call"}
 
     if rank != 0:
         if dist is not None:
@@ -380,6 +421,8 @@ def main():
         # batch for the 16-bit forms
         "gpu_launches": sum(v["launches"] * (1 if kk == "f32" else 2) for kk, v in kernel.items()),
         "cpu_baseline": cpu,
+        "paths": {kk: path_taken.get(kk) for kk in forms},
+        **extra,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -77,10 +77,15 @@ typedef enum {
     BP_OPT_LANES_X = 4,
     /* Data path of the backprojection: 0 (default) automatic, 1 texture
      * gathers, 2 TMA-staged shared-memory tiles.  Both give identical
-     * volumes; the automatic choice takes the TMA path when the footprint of
-     * a 16 x 8 x 8 voxel brick fits its tile for every projection of the
-     * batch.  bp_query(BP_QUERY_LAST_PATH) reports the path taken. */
-    BP_OPT_PATH = 5
+     * volumes; the automatic choice is the texture path (with BP_OPT_CULL),
+     * the faster of the two on GB300 for every storage type.
+     * bp_query(BP_QUERY_LAST_PATH) reports the path taken. */
+    BP_OPT_PATH = 5,
+    /* 1 (default): skip, per block of voxels, the projections whose footprint
+     * misses the detector (the line-wise clipping of Sect. 3.3 at block
+     * granularity; the skipped terms are exactly zero, so the volume is
+     * bit-identical); 0: compute every term. */
+    BP_OPT_CULL = 6
 } bp_option;
 
 /* Queries for bp_query. */

@@ -77,6 +77,9 @@ struct bp_ctx {
     size_t pair_slot_bytes = 0;
     CUtensorMap maps[2][kMaxBatch];
     int *err_dev = nullptr;        // set by a kernel whose bounded wait gave up
+    bool cull = true;              // BP_OPT_CULL
+    unsigned long long *masks = nullptr;   // per-block visibility masks (texture path)
+    long long mask_blocks = 0;
     size_t ev_used = 0;
     char err[1024] = "no error";
 };
@@ -134,6 +137,8 @@ static void release(bp_ctx *c)
         cudaFree(c->vol);
     if (c->err_dev)
         cudaFree(c->err_dev);
+    if (c->masks)
+        cudaFree(c->masks);
     if (c->copy_stream)
         cudaStreamDestroy(c->copy_stream);
 }
@@ -260,6 +265,11 @@ extern "C" bp_status bp_set_option(bp_ctx *c, int option, long long value)
             return fail(c, BP_EINVAL, "bp_set_option: LANES_X takes 8, 16, 32, 44, 42, 82 or 24");
         c->lanes_x = (int)value;
         return BP_OK;
+    case BP_OPT_CULL:
+        if (value != 0 && value != 1)
+            return fail(c, BP_EINVAL, "bp_set_option: CULL takes 0 or 1");
+        c->cull = value != 0;
+        return BP_OK;
     case BP_OPT_PATH:
         if (value < 0 || value > 2)
             return fail(c, BP_EINVAL, "bp_set_option: PATH takes 0 (auto), 1 (texture) or 2 (TMA)");
@@ -381,54 +391,6 @@ static bp_status ensure_pairs(bp_ctx *c)
     return BP_OK;
 }
 
-// Host estimate for the automatic path choice: do at least half of the
-// footprints of the 8 bricks at the volume's corners (the most magnified
-// ones), over the batch's projections, fit the TMA box?  Then nearly all
-// bricks fit, and the few that do not take the kernel's global-memory path,
-// so this only picks the faster kernel, never a wrong one.
-static bool tma_fits(const bp_ctx *c, const double *A, int n)
-{
-    const int kind = pair_kind(c);
-    const int BU = kind == kPairF32 ? TmaBox<kPairF32>::BU : TmaBox<kPairF16>::BU;
-    const int BV = kind == kPairF32 ? TmaBox<kPairF32>::BV : TmaBox<kPairF16>::BV;
-    const int align = kind == kPairF32 ? 2 : 4;
-    const int L = c->L;
-    const int bl[3] = {kBrickX, kBrickY, kBrickZ};
-    long long fit = 0, total = 0;
-    for (int i = 0; i < n; ++i) {
-        const double *a = A + 12 * (size_t)i;
-        for (int corner = 0; corner < 8; ++corner) {
-            int lo[3], hi[3];
-            for (int d = 0; d < 3; ++d) {
-                const bool up = (corner >> d) & 1;
-                const int first = up ? (L - 1) / bl[d] * bl[d] : 0;
-                lo[d] = first;
-                hi[d] = std::min(first + bl[d], L) - 1;
-            }
-            double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
-            for (int q = 0; q < 8; ++q) {
-                const double X = c->O[0] + c->R * ((q & 1) ? hi[0] : lo[0]);
-                const double Y = c->O[1] + c->R * ((q & 2) ? hi[1] : lo[1]);
-                const double Z = c->O[2] + c->R * ((q & 4) ? hi[2] : lo[2]);
-                const double w = a[8] * X + a[9] * Y + a[10] * Z + a[11];
-                const double u = (a[0] * X + a[1] * Y + a[2] * Z + a[3]) / w;
-                const double v = (a[4] * X + a[5] * Y + a[6] * Z + a[7]) / w;
-                umin = std::min(umin, u);
-                umax = std::max(umax, u);
-                vmin = std::min(vmin, v);
-                vmax = std::max(vmax, v);
-            }
-            // the kernel's margins (one pixel each side), alignment slack, and
-            // one more pixel for float32 rounding
-            ++total;
-            if (std::floor(umax) - std::floor(umin) + 3 + (align - 1) + 1 <= BU - 1 &&
-                std::floor(vmax) - std::floor(vmin) + 4 + 1 <= BV - 1)
-                ++fit;
-        }
-    }
-    return 2 * fit >= total;
-}
-
 static bp_status record_start(bp_ctx *c, cudaEvent_t *stop)
 {
     *stop = nullptr;
@@ -470,7 +432,10 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
     for (int c0 = 0; c0 < n; c0 += c->batch) {
         const int m = n - c0 < c->batch ? n - c0 : c->batch;
         const double *A0 = A + 12 * (size_t)c0;
-        const bool tma = c->path == 2 || (c->path == 0 && tma_fits(c, A0, m));
+        // Automatic choice: the texture path with block culling (measured
+        // faster than the TMA path for every storage type on GB300); the TMA
+        // path only on request.
+        const bool tma = c->path == 2;
         if (tma) {
             st = ensure_pairs(c);
             if (st != BP_OK)
@@ -551,8 +516,22 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 b.k[j] = make_float2((float)ku, (float)kv);
                 b.tex[j] = c->tex[s][j];
             }
+            unsigned long long *masks = nullptr;
+            if (c->cull) {
+                const long long nb = fwd_blocks(c->L, c->lanes_x);
+                if (nb > c->mask_blocks) {
+                    if (c->masks)
+                        CTX_CK(c, cudaFree(c->masks));
+                    c->masks = nullptr;
+                    c->mask_blocks = 0;
+                    CTX_CK(c, cudaMalloc((void **)&c->masks, sizeof(unsigned long long) * nb));
+                    c->mask_blocks = nb;
+                }
+                masks = c->masks;
+                CTX_CK(c, launch_cull_masks(b, g, c->isx, c->isy, c->lanes_x, masks, c->stream));
+            }
             CTX_CK(c, launch_bp_fwd(b, c->vol, g, c->dtype == BP_BF16 ? kTexBF16 : kTexFloat, !c->vol_zero,
-                                    c->ieee_rcp, c->lanes_x, c->stream));
+                                    c->ieee_rcp, c->lanes_x, masks, c->stream));
         }
         if (ev_stop)
             CTX_CK(c, cudaEventRecord(ev_stop, c->stream));

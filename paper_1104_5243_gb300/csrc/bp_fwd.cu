@@ -28,6 +28,11 @@
 //    whole 32-byte sectors.
 //  * The matrices and texture handles of the batch are kernel parameters,
 //    read through the constant cache with a warp-uniform index.
+//  * Brick culling (the line-wise clipping of Sect. 3.3 at block
+//    granularity): a pre-pass marks, per thread block, the projections whose
+//    footprint can reach the block's voxels; the others are skipped with a
+//    block-uniform branch.  Skipped terms are exactly zero, so culling does
+//    not change a single bit of the volume.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -65,7 +70,7 @@ __device__ __forceinline__ float4 gather(cudaTextureObject_t t, float x, float y
 template <int KIND, bool IEEE, int LX, int LY>
 __global__ void __launch_bounds__(kThreads, 6)
 bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const VolGeom g,
-              int accumulate)
+              int accumulate, const unsigned long long *__restrict__ masks)
 {
     constexpr int LZ = 32 / (LX * LY);          // lanes along z
     constexpr int TX = LX * kVoxPerLane;        // x extent of the block tile
@@ -89,8 +94,13 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
 #pragma unroll
     for (int k = 0; k < kVoxPerLane; ++k)
         acc[k] = 0.f;
+    // projections that can reach this block (all of them without culling)
+    const unsigned long long visible =
+        masks ? masks[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] : ~0ull;
 #pragma unroll 1
     for (int i = 0; i < b.n; ++i) {
+        if (!((visible >> i) & 1ull))
+            continue;   // every term of this projection is exactly zero here
         const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
         const float2 kc = b.k[i];
         const cudaTextureObject_t t = b.tex[i];
@@ -126,12 +136,94 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
     }
 }
 
+// Block tile of a layout: (TX, TY, TZ) voxels.
+static void layout_tile(int lanes_x, int *tx, int *ty, int *tz)
+{
+    int lx = 8, ly = 1;
+    switch (lanes_x) {
+    case 32: lx = 32; break;
+    case 16: lx = 16; break;
+    case 44: lx = 4; ly = 4; break;
+    case 42: lx = 4; ly = 2; break;
+    case 82: lx = 8; ly = 2; break;
+    case 24: lx = 2; ly = 4; break;
+    default: break;
+    }
+    *tx = lx * kVoxPerLane;
+    *ty = kWarpsY * ly;
+    *tz = 32 / (lx * ly);
+}
+
+long long fwd_blocks(int L, int lanes_x)
+{
+    int tx, ty, tz;
+    layout_tile(lanes_x, &tx, &ty, &tz);
+    return (long long)((L + tx - 1) / tx) * ((L + ty - 1) / ty) * ((L + tz - 1) / tz);
+}
+
 template <int KIND, bool IEEE, int LX, int LY>
-static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bool acc, cudaStream_t s)
+static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bool acc,
+                             const unsigned long long *masks, cudaStream_t s)
 {
     constexpr int TX = LX * kVoxPerLane, TY = kWarpsY * LY, LZ = 32 / (LX * LY);
     dim3 grid((g.L + TX - 1) / TX, (g.L + TY - 1) / TY, (g.L + LZ - 1) / LZ);
-    bp_fwd_kernel<KIND, IEEE, LX, LY><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0);
+    bp_fwd_kernel<KIND, IEEE, LX, LY><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0, masks);
+    return cudaGetLastError();
+}
+
+// One thread per block of the texture kernel: project the 8 corners of the
+// block's voxel box (clamped to the volume) for every projection of the
+// batch, with the kernel's float32 arithmetic, and keep the projection when
+// the footprint, widened by one pixel, touches [-1, isx] x [-1, isy].
+__global__ void __launch_bounds__(256)
+cull_mask_kernel(const __grid_constant__ FwdBatch b, const VolGeom g, int isx, int isy, int tx, int ty,
+                 int tz, int nbx, int nby, long long nblocks, unsigned long long *__restrict__ masks)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nblocks)
+        return;
+    const int bx = (int)(q % nbx), by = (int)((q / nbx) % nby), bz = (int)(q / ((long long)nbx * nby));
+    const int x0 = bx * tx, y0 = by * ty, z0 = bz * tz;
+    const int x1 = min(x0 + tx, g.L) - 1, y1 = min(y0 + ty, g.L) - 1, z1 = min(z0 + tz, g.L) - 1;
+    unsigned long long m = 0;
+    for (int i = 0; i < b.n; ++i) {
+        const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+        float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float X = fmaf(g.R, (float)((c & 1) ? x1 : x0), g.Ox);
+            const float Y = fmaf(g.R, (float)((c & 2) ? y1 : y0), g.Oy);
+            const float Z = fmaf(g.R, (float)((c & 4) ? z1 : z0), g.Oz);
+            const float w = fmaf(rw.x, X, fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w)));
+            const float r = 1.0f / w;
+            const float u = fmaf(ru.x, X, fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w))) * r;
+            const float v = fmaf(rv.x, X, fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w))) * r;
+            umin = fminf(umin, u);
+            umax = fmaxf(umax, u);
+            vmin = fminf(vmin, v);
+            vmax = fmaxf(vmax, v);
+        }
+        // centred coordinates: pixel u = u' + ku - 1; keep unless the box,
+        // widened by a pixel, lies entirely left of -1 or right of isx
+        const float2 kc = b.k[i];
+        const float pu0 = umin + kc.x - 2.f, pu1 = umax + kc.x;
+        const float pv0 = vmin + kc.y - 2.f, pv1 = vmax + kc.y;
+        const bool miss = pu1 < -1.f || pu0 > (float)isx || pv1 < -1.f || pv0 > (float)isy;
+        if (!miss)
+            m |= 1ull << i;
+    }
+    masks[q] = m;
+}
+
+cudaError_t launch_cull_masks(const FwdBatch &b, const VolGeom &g, int isx, int isy, int lanes_x,
+                              unsigned long long *masks, cudaStream_t s)
+{
+    int tx, ty, tz;
+    layout_tile(lanes_x, &tx, &ty, &tz);
+    const int nbx = (g.L + tx - 1) / tx, nby = (g.L + ty - 1) / ty;
+    const long long nblocks = fwd_blocks(g.L, lanes_x);
+    cull_mask_kernel<<<(unsigned)((nblocks + 255) / 256), 256, 0, s>>>(b, g, isx, isy, tx, ty, tz, nbx, nby,
+                                                                      nblocks, masks);
     return cudaGetLastError();
 }
 
@@ -140,29 +232,30 @@ static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bo
 // (the rest along z): 44, 42, 82, 24.
 template <int KIND, bool IEEE>
 static cudaError_t launch_kind(const FwdBatch &b, float *vol, const VolGeom &g, bool acc, int layout,
-                               cudaStream_t s)
+                               const unsigned long long *m, cudaStream_t s)
 {
     switch (layout) {
-    case 32: return launch_lx<KIND, IEEE, 32, 1>(b, vol, g, acc, s);
-    case 16: return launch_lx<KIND, IEEE, 16, 1>(b, vol, g, acc, s);
-    case 44: return launch_lx<KIND, IEEE, 4, 4>(b, vol, g, acc, s);
-    case 42: return launch_lx<KIND, IEEE, 4, 2>(b, vol, g, acc, s);
-    case 82: return launch_lx<KIND, IEEE, 8, 2>(b, vol, g, acc, s);
-    case 24: return launch_lx<KIND, IEEE, 2, 4>(b, vol, g, acc, s);
-    default: return launch_lx<KIND, IEEE, 8, 1>(b, vol, g, acc, s);
+    case 32: return launch_lx<KIND, IEEE, 32, 1>(b, vol, g, acc, m, s);
+    case 16: return launch_lx<KIND, IEEE, 16, 1>(b, vol, g, acc, m, s);
+    case 44: return launch_lx<KIND, IEEE, 4, 4>(b, vol, g, acc, m, s);
+    case 42: return launch_lx<KIND, IEEE, 4, 2>(b, vol, g, acc, m, s);
+    case 82: return launch_lx<KIND, IEEE, 8, 2>(b, vol, g, acc, m, s);
+    case 24: return launch_lx<KIND, IEEE, 2, 4>(b, vol, g, acc, m, s);
+    default: return launch_lx<KIND, IEEE, 8, 1>(b, vol, g, acc, m, s);
     }
 }
 
 cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int tex_kind,
-                          bool accumulate, bool ieee_rcp, int lanes_x, cudaStream_t s)
+                          bool accumulate, bool ieee_rcp, int lanes_x, const unsigned long long *masks,
+                          cudaStream_t s)
 {
     if (b.n <= 0)
         return cudaSuccess;
     if (tex_kind == kTexFloat)
-        return ieee_rcp ? launch_kind<kTexFloat, true>(b, vol, g, accumulate, lanes_x, s)
-                        : launch_kind<kTexFloat, false>(b, vol, g, accumulate, lanes_x, s);
-    return ieee_rcp ? launch_kind<kTexBF16, true>(b, vol, g, accumulate, lanes_x, s)
-                    : launch_kind<kTexBF16, false>(b, vol, g, accumulate, lanes_x, s);
+        return ieee_rcp ? launch_kind<kTexFloat, true>(b, vol, g, accumulate, lanes_x, masks, s)
+                        : launch_kind<kTexFloat, false>(b, vol, g, accumulate, lanes_x, masks, s);
+    return ieee_rcp ? launch_kind<kTexBF16, true>(b, vol, g, accumulate, lanes_x, masks, s)
+                    : launch_kind<kTexBF16, false>(b, vol, g, accumulate, lanes_x, masks, s);
 }
 
 // ---------------------------------------------------------------------------

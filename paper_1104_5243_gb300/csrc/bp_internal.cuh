@@ -54,8 +54,20 @@ struct VolGeom {
 // unit widens FP16 exactly) or raw 16-bit words holding BF16.
 enum TexKind { kTexFloat = 0, kTexBF16 = 1 };
 
+// masks: one 64-bit word per thread block of the texture kernel, bit i set
+// when projection i of the batch can reach the block's voxels (NULL: no
+// culling).  Built by launch_cull_masks for the same layout.
 cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int tex_kind,
-                          bool accumulate, bool ieee_rcp, int lanes_x, cudaStream_t s);
+                          bool accumulate, bool ieee_rcp, int lanes_x, const unsigned long long *masks,
+                          cudaStream_t s);
+
+// Number of thread blocks of the texture kernel for a layout, and the mask
+// pre-pass: a block's bit for projection i is cleared when the projections
+// of its voxel box miss the detector by more than a pixel (every term of
+// those updates is exactly zero).
+long long fwd_blocks(int L, int lanes_x);
+cudaError_t launch_cull_masks(const FwdBatch &b, const VolGeom &g, int isx, int isy, int lanes_x,
+                              unsigned long long *masks, cudaStream_t s);
 
 cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom &g,
                               float *out, int isx, int isy, bool ieee_rcp, cudaStream_t s);
@@ -78,8 +90,9 @@ template <> struct TmaBox<kPairBF16> { static constexpr int BU = 68, BV = 32; };
 // box origin on a 16-byte boundary.
 template <int KIND> constexpr int kPairWords = KIND == kPairF32 ? 2 : 1;
 template <int KIND> constexpr int kPairAlign = KIND == kPairF32 ? 2 : 4;
-constexpr int kTmaWaitIters = 1 << 22;
-constexpr int kTmaStages = 3;   // depth of the shared-memory ring
+constexpr int kTmaWaitIters = 1 << 14;          // bounded waits: at most ~2 s
+constexpr unsigned kTmaSuspendNs = 100000;        // suspend hint per try, ns
+constexpr int kTmaStages = 3;                     // depth of the shared-memory ring
 
 struct TmaBatch {
     CUtensorMap map[kMaxBatch];        // one per projection's pair image

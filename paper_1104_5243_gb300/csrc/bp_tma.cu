@@ -61,20 +61,22 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+// try_wait with a suspend-time hint: a waiting warp sleeps (for at most
+// the hint) until the phase completes instead of spinning on issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kTmaSuspendNs)
         : "memory");
     return done != 0;
 }
 
-// Bounded wait: about a second at most (try_wait itself suspends briefly).
+// Bounded wait: at most kTmaWaitIters suspensions of kTmaSuspendNs each.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
     for (int it = 0; it < kTmaWaitIters; ++it)
@@ -151,8 +153,10 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     extern __shared__ __align__(128) unsigned char dyn_smem[];   // the ring: S stages of kBufElems pairs
     T (*buf)[kBufElems] = reinterpret_cast<T (*)[kBufElems]>(dyn_smem);
     __shared__ __align__(8) uint64_t full[S], empty[S];
-    // per stage: mode (0 culled, 1 shared memory, 2 global) and box origin
-    __shared__ int meta_mode[S], meta_cx0[S], meta_ry0[S];
+    // per stage: mode (0 culled, 1 shared memory, 2 global) and the column /
+    // row offsets that turn floor(u'), floor(v') into indices of the staged
+    // box (mode 1) or of the global pair image (mode 2)
+    __shared__ int4 meta[S];
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -219,10 +223,10 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                     cx0 = cmin & ~(kPairAlign<KIND> - 1);
                     ry0 = rmin;
                     mode = (cmax < cx0 + BU && rmax < ry0 + BV) ? 1 : 2;
+                    if (mode == 2)
+                        cx0 = ry0 = 0;   // the global path indexes the whole pair image
                 }
-                meta_mode[st] = mode;
-                meta_cx0[st] = cx0;
-                meta_ry0[st] = ry0;
+                meta[st] = make_int4(mode, kc.x - cx0, kc.y - 1 - ry0, 0);
                 if (mode == 1) {
                     mbar_expect_tx(&full[st], (uint32_t)(kBufElems * sizeof(T)));   // also publishes meta
                     tma_load_2d(buf[st], &b.map[i], cx0 * kPairWords<KIND>, ry0, &full[st]);
@@ -265,14 +269,10 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
             ok = false;
             break;
         }
-        const int mode = meta_mode[s];
+        const int4 mt = meta[s];
+        const int mode = mt.x, cu = mt.y, cv = mt.z;
         if (mode != 0) {
             const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
-            const int2 kc = b.k[i];
-            // column / row offsets that turn floor(u'), floor(v') into
-            // indices of the staged box (or of the global pair image)
-            const int cu = kc.x - (mode == 1 ? meta_cx0[s] : 0);
-            const int cv = kc.y - 1 - (mode == 1 ? meta_ry0[s] : 0);
 #pragma unroll
             for (int kz = 0; kz < 2; ++kz) {
                 const float bu = fmaf(ru.y, Y, fmaf(ru.z, Zv[kz], ru.w));
@@ -293,7 +293,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                         // the corner-based box covers every voxel of the
                         // volume with a pixel of margin; the clamp only
                         // guards the array for lanes beyond a ragged edge
-                        const int idx = min(max(row * BU + col, 0), kBufElems - BU - 1);
+                        const int idx = (int)min((unsigned)(row * BU + col), (unsigned)(kBufElems - BU - 1));
                         const T *p = buf[s] + idx;
                         top = P::unpack(p[0]);
                         bot = P::unpack(p[BU]);
