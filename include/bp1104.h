@@ -91,7 +91,9 @@ typedef enum {
 /* Queries for bp_query. */
 typedef enum {
     BP_QUERY_LAST_PATH = 1,          /* data path of the last batch: 1 texture, 2 TMA, 0 none yet */
-    BP_QUERY_PROJECTIONS_ADDED = 2   /* projections accumulated since create / reset / set_state */
+    BP_QUERY_PROJECTIONS_ADDED = 2,  /* projections accumulated since create / reset / set_state */
+    BP_QUERY_UPDATES_COMPUTED = 3    /* voxel updates actually computed since create (culled blocks
+                                      * excluded; synchronises the stream) */
 } bp_query_what;
 
 /* ---------------------------------------------------------------- context */
@@ -159,7 +161,7 @@ bp_status bp_adjoint(bp_ctx *ctx, const float *vol, int vol_on_device,
                      const double *A, int n, float *images_out, int out_on_device);
 
 /* Read a bp_query_what value into *value.  BP_EINVAL for an unknown query. */
-bp_status bp_query(const bp_ctx *ctx, int what, long long *value);
+bp_status bp_query(bp_ctx *ctx, int what, long long *value);
 
 /* Device time of the backprojection kernel launches recorded while
  * BP_OPT_TIMING was on (measurement support, in the spirit of the paper's

@@ -85,6 +85,7 @@ class Backprojector:
         N.bp_reset(self._ctx)
 
     def query(self, what: int) -> int:
+        """bp_query: N.BP_QUERY_LAST_PATH, _PROJECTIONS_ADDED, _UPDATES_COMPUTED."""
         return N.bp_query(self._ctx, what)
 
     @property

@@ -78,6 +78,8 @@ struct bp_ctx {
     CUtensorMap maps[2][kMaxBatch];
     int *err_dev = nullptr;        // set by a kernel whose bounded wait gave up
     bool cull = true;              // BP_OPT_CULL
+    unsigned long long *work_dev = nullptr;   // updates computed by culled launches
+    unsigned long long work_host = 0;         // updates of launches without culling
     unsigned long long *masks = nullptr;   // per-block visibility masks (texture path)
     long long mask_blocks = 0;
     size_t ev_used = 0;
@@ -139,6 +141,8 @@ static void release(bp_ctx *c)
         cudaFree(c->err_dev);
     if (c->masks)
         cudaFree(c->masks);
+    if (c->work_dev)
+        cudaFree(c->work_dev);
     if (c->copy_stream)
         cudaStreamDestroy(c->copy_stream);
 }
@@ -212,6 +216,9 @@ extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
     check(cudaMalloc((void **)&c->err_dev, sizeof(int)), "cudaMalloc(error flag)");
     if (st == BP_OK)
         check(cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream), "cudaMemsetAsync");
+    check(cudaMalloc((void **)&c->work_dev, sizeof(unsigned long long)), "cudaMalloc(work counter)");
+    if (st == BP_OK)
+        check(cudaMemsetAsync(c->work_dev, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync");
     if (st == BP_OK)
         check(cudaMemsetAsync(c->vol, 0, nvox * sizeof(float), c->stream), "cudaMemsetAsync");
     for (int s = 0; s < 2 && st == BP_OK; ++s)
@@ -501,7 +508,8 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 tb.map[j] = c->maps[s][j];
                 tb.img[j] = static_cast<const char *>(c->pairs[s]) + c->pair_slot_bytes * j;
             }
-            CTX_CK(c, launch_bp_tma(tb, c->vol, g, pair_kind(c), !c->vol_zero, c->ieee_rcp, c->err_dev, c->stream));
+            CTX_CK(c, launch_bp_tma(tb, c->vol, g, pair_kind(c), !c->vol_zero, c->ieee_rcp, c->err_dev, c->work_dev,
+                                    c->stream));
         } else {
             FwdBatch b;
             b.n = m;
@@ -528,7 +536,9 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                     c->mask_blocks = nb;
                 }
                 masks = c->masks;
-                CTX_CK(c, launch_cull_masks(b, g, c->isx, c->isy, c->lanes_x, masks, c->stream));
+                CTX_CK(c, launch_cull_masks(b, g, c->isx, c->isy, c->lanes_x, masks, c->work_dev, c->stream));
+            } else {
+                c->work_host += (unsigned long long)m * c->L * c->L * c->L;
             }
             CTX_CK(c, launch_bp_fwd(b, c->vol, g, c->dtype == BP_BF16 ? kTexBF16 : kTexFloat, !c->vol_zero,
                                     c->ieee_rcp, c->lanes_x, masks, c->stream));
@@ -557,7 +567,7 @@ static bp_status check_device_error(bp_ctx *c, const char *who)
     return BP_OK;
 }
 
-extern "C" bp_status bp_query(const bp_ctx *c, int what, long long *value)
+extern "C" bp_status bp_query(bp_ctx *c, int what, long long *value)
 {
     if (c == nullptr || value == nullptr)
         return fail(nullptr, BP_EINVAL, "bp_query: NULL argument");
@@ -568,6 +578,16 @@ extern "C" bp_status bp_query(const bp_ctx *c, int what, long long *value)
     case BP_QUERY_PROJECTIONS_ADDED:
         *value = c->n_added;
         return BP_OK;
+    case BP_QUERY_UPDATES_COMPUTED: {
+        unsigned long long dev = 0;
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(&dev, c->work_dev, sizeof dev, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return fail(nullptr, BP_ECUDA, "bp_query: %s", cudaGetErrorString(e));
+        *value = (long long)(dev + c->work_host);
+        return BP_OK;
+    }
     default:
         return fail(nullptr, BP_EINVAL, "bp_query: unknown query %d", what);
     }

@@ -171,20 +171,14 @@ static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bo
     return cudaGetLastError();
 }
 
-// One thread per block of the texture kernel: project the 8 corners of the
-// block's voxel box (clamped to the volume) for every projection of the
-// batch, with the kernel's float32 arithmetic, and keep the projection when
-// the footprint, widened by one pixel, touches [-1, isx] x [-1, isy].
-__global__ void __launch_bounds__(256)
-cull_mask_kernel(const __grid_constant__ FwdBatch b, const VolGeom g, int isx, int isy, int tx, int ty,
-                 int tz, int nbx, int nby, long long nblocks, unsigned long long *__restrict__ masks)
+// Visibility mask of one thread block of the texture kernel: project the 8
+// corners of the block's voxel box (clamped to the volume) for every
+// projection of the batch, with the kernel's float32 arithmetic, and keep
+// the projection when the footprint, widened by one pixel, touches
+// [-1, isx] x [-1, isy].  Returns the number of voxel updates it keeps.
+__device__ unsigned long long block_mask(const FwdBatch &b, const VolGeom &g, int isx, int isy, int x0, int y0,
+                                         int z0, int x1, int y1, int z1, unsigned long long *mask)
 {
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nblocks)
-        return;
-    const int bx = (int)(q % nbx), by = (int)((q / nbx) % nby), bz = (int)(q / ((long long)nbx * nby));
-    const int x0 = bx * tx, y0 = by * ty, z0 = bz * tz;
-    const int x1 = min(x0 + tx, g.L) - 1, y1 = min(y0 + ty, g.L) - 1, z1 = min(z0 + tz, g.L) - 1;
     unsigned long long m = 0;
     for (int i = 0; i < b.n; ++i) {
         const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
@@ -212,18 +206,40 @@ cull_mask_kernel(const __grid_constant__ FwdBatch b, const VolGeom g, int isx, i
         if (!miss)
             m |= 1ull << i;
     }
-    masks[q] = m;
+    *mask = m;
+    return (unsigned long long)__popcll(m) * (x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1);
+}
+
+// One thread per block of the texture kernel; the kept updates are summed
+// per warp into the context's work counter (for the roofline).
+__global__ void __launch_bounds__(256)
+cull_mask_kernel(const __grid_constant__ FwdBatch b, const VolGeom g, int isx, int isy, int tx, int ty,
+                 int tz, int nbx, int nby, long long nblocks, unsigned long long *__restrict__ masks,
+                 unsigned long long *__restrict__ work)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long done = 0;
+    if (q < nblocks) {
+        const int bx = (int)(q % nbx), by = (int)((q / nbx) % nby), bz = (int)(q / ((long long)nbx * nby));
+        const int x0 = bx * tx, y0 = by * ty, z0 = bz * tz;
+        done = block_mask(b, g, isx, isy, x0, y0, z0, min(x0 + tx, g.L) - 1, min(y0 + ty, g.L) - 1,
+                          min(z0 + tz, g.L) - 1, &masks[q]);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        done += __shfl_down_sync(0xffffffffu, done, o);
+    if ((threadIdx.x & 31) == 0 && done)
+        atomicAdd(work, done);
 }
 
 cudaError_t launch_cull_masks(const FwdBatch &b, const VolGeom &g, int isx, int isy, int lanes_x,
-                              unsigned long long *masks, cudaStream_t s)
+                              unsigned long long *masks, unsigned long long *work, cudaStream_t s)
 {
     int tx, ty, tz;
     layout_tile(lanes_x, &tx, &ty, &tz);
     const int nbx = (g.L + tx - 1) / tx, nby = (g.L + ty - 1) / ty;
     const long long nblocks = fwd_blocks(g.L, lanes_x);
     cull_mask_kernel<<<(unsigned)((nblocks + 255) / 256), 256, 0, s>>>(b, g, isx, isy, tx, ty, tz, nbx, nby,
-                                                                      nblocks, masks);
+                                                                      nblocks, masks, work);
     return cudaGetLastError();
 }
 

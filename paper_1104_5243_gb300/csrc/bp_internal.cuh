@@ -67,7 +67,7 @@ cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int t
 // those updates is exactly zero).
 long long fwd_blocks(int L, int lanes_x);
 cudaError_t launch_cull_masks(const FwdBatch &b, const VolGeom &g, int isx, int isy, int lanes_x,
-                              unsigned long long *masks, cudaStream_t s);
+                              unsigned long long *masks, unsigned long long *work, cudaStream_t s);
 
 cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom &g,
                               float *out, int isx, int isy, bool ieee_rcp, cudaStream_t s);
@@ -103,7 +103,7 @@ struct TmaBatch {
 };
 
 cudaError_t launch_bp_tma(const TmaBatch &b, float *vol, const VolGeom &g, int pair_kind, bool accumulate,
-                          bool ieee_rcp, int *err, cudaStream_t s);
+                          bool ieee_rcp, int *err, unsigned long long *work, cudaStream_t s);
 
 struct PairBatch {
     const float *src[kMaxBatch];

@@ -142,7 +142,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 template <int KIND, bool IEEE>
 __global__ void __launch_bounds__(kThreads + 32, 4)
 bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const VolGeom g, int accumulate,
-              int *__restrict__ err)
+              int *__restrict__ err, unsigned long long *__restrict__ work)
 {
     using P = Pairs<KIND>;
     using T = typename P::T;
@@ -181,6 +181,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
         const float Yc = fmaf(g.R, (float)((c & 2) ? ye : by0), g.Oy);
         const float Z = fmaf(g.R, (float)((c & 4) ? ze : bz0), g.Oz);
         int issued = 0;            // stages whose tile may still be in flight
+        unsigned long long computed = 0;   // projections this brick computes
         int last_use[S] = {};      // use index of each stage's last tile
         for (int i = 0; i < b.n; ++i) {
             const int st = i % S, use = i / S;
@@ -227,6 +228,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                         cx0 = ry0 = 0;   // the global path indexes the whole pair image
                 }
                 meta[st] = make_int4(mode, kc.x - cx0, kc.y - 1 - ry0, 0);
+                computed += mode != 0;
                 if (mode == 1) {
                     mbar_expect_tx(&full[st], (uint32_t)(kBufElems * sizeof(T)));   // also publishes meta
                     tma_load_2d(buf[st], &b.map[i], cx0 * kPairWords<KIND>, ry0, &full[st]);
@@ -239,6 +241,8 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
             }
             __syncwarp();
         }
+        if (lane == 0 && computed)
+            atomicAdd(work, computed * (unsigned long long)((xe - bx0 + 1) * (ye - by0 + 1) * (ze - bz0 + 1)));
         if (lane == 0 && *(volatile int *)&abort_flag) {
             // let copies still in flight land before the block's memory goes away
             for (int q = 0; q < S; ++q)
@@ -339,7 +343,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
 
 template <int KIND, bool IEEE>
 static cudaError_t launch_tma_kind(const TmaBatch &b, float *vol, const VolGeom &g, bool acc, int *err,
-                                   cudaStream_t s)
+                                   unsigned long long *work, cudaStream_t s)
 {
     dim3 grid((g.L + kBrickX - 1) / kBrickX, (g.L + kBrickY - 1) / kBrickY, (g.L + kBrickZ - 1) / kBrickZ);
     using T = typename Pairs<KIND>::T;
@@ -350,25 +354,25 @@ static cudaError_t launch_tma_kind(const TmaBatch &b, float *vol, const VolGeom 
                                          (int)smem);
     if (e != cudaSuccess)
         return e;
-    bp_tma_kernel<KIND, IEEE><<<grid, kThreads + 32, smem, s>>>(b, vol, g, acc ? 1 : 0, err);
+    bp_tma_kernel<KIND, IEEE><<<grid, kThreads + 32, smem, s>>>(b, vol, g, acc ? 1 : 0, err, work);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bp_tma(const TmaBatch &b, float *vol, const VolGeom &g, int pair_kind, bool accumulate,
-                          bool ieee_rcp, int *err, cudaStream_t s)
+                          bool ieee_rcp, int *err, unsigned long long *work, cudaStream_t s)
 {
     if (b.n <= 0)
         return cudaSuccess;
     switch (pair_kind) {
     case kPairF32:
-        return ieee_rcp ? launch_tma_kind<kPairF32, true>(b, vol, g, accumulate, err, s)
-                        : launch_tma_kind<kPairF32, false>(b, vol, g, accumulate, err, s);
+        return ieee_rcp ? launch_tma_kind<kPairF32, true>(b, vol, g, accumulate, err, work, s)
+                        : launch_tma_kind<kPairF32, false>(b, vol, g, accumulate, err, work, s);
     case kPairF16:
-        return ieee_rcp ? launch_tma_kind<kPairF16, true>(b, vol, g, accumulate, err, s)
-                        : launch_tma_kind<kPairF16, false>(b, vol, g, accumulate, err, s);
+        return ieee_rcp ? launch_tma_kind<kPairF16, true>(b, vol, g, accumulate, err, work, s)
+                        : launch_tma_kind<kPairF16, false>(b, vol, g, accumulate, err, work, s);
     default:
-        return ieee_rcp ? launch_tma_kind<kPairBF16, true>(b, vol, g, accumulate, err, s)
-                        : launch_tma_kind<kPairBF16, false>(b, vol, g, accumulate, err, s);
+        return ieee_rcp ? launch_tma_kind<kPairBF16, true>(b, vol, g, accumulate, err, work, s)
+                        : launch_tma_kind<kPairBF16, false>(b, vol, g, accumulate, err, work, s);
     }
 }
 
