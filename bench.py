@@ -160,6 +160,23 @@ def gpu_id_for_smi(torch, dev: int) -> str | None:
 
 
 # ---------------------------------------------------------------------------
+# Multi-rank bookkeeping (one process per GPU, independent reconstructions,
+# no data-path collective): the slowest rank's time decides, and the value is
+# the work of all ranks over that time.
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gups(updates_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """GUP/s of the whole job: every rank's updates over the slowest rank's time."""
+    return updates_per_rank * steps * world / (max_ms / 1e3) / 1e9
+
+
 def cpu_baseline(L: int, n_sample: int):
     """The FP64 oracle (as it stands) on a bounded sample of the workload: the
     full L^3 volume backprojected from the first n_sample projections, with
@@ -262,12 +279,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x: float) -> float:
+        return max_over_ranks(x, dist, "cuda")
 
     smi_id = gpu_id_for_smi(torch, local_rank)
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
@@ -299,12 +312,12 @@ def main():
                 step()
             t1.record(stream)
             torch.cuda.synchronize()
-        ms = max_over_ranks(t0.elapsed_time(t1))
+        ms = rank_max(t0.elapsed_time(t1))
         launches, kms = bp.kernel_stats()
         computed = bp.query(N.BP_QUERY_UPDATES_COMPUTED) - computed0
         path_taken[form] = bp.last_path
         bp.set_option(N.BP_OPT_TIMING, 0)
-        gups = updates * args.steps * world / (ms / 1e3) / 1e9
+        gups = whole_job_gups(updates, args.steps, world, ms)
         forms[form] = {"value": round(gups, 2), "ms_per_step": round(ms / args.steps, 3)}
         kernel[form] = {"launches": launches, "kernel_ms": kms,
                         "kernel_gups": updates * args.steps / (kms / 1e3) / 1e9 if kms > 0 else None,
@@ -333,9 +346,9 @@ def main():
         for _ in range(args.steps):
             step_e2e()
         torch.cuda.synchronize()
-        wall = max_over_ranks(time.perf_counter() - t0)
+        wall = rank_max(time.perf_counter() - t0)
         bp.close()
-        e2e = {"value": round(updates * args.steps * world / wall / 1e9, 2), "unit": UNIT,
+        e2e = {"value": round(whole_job_gups(updates, args.steps, world, wall * 1e3), 2), "unit": UNIT,
                "h2d_bytes_per_step": int(stack_host.numel() * 4),
                "d2h_bytes_per_step": int(vol_host.numel() * 4)}
 

@@ -84,7 +84,9 @@ typedef enum {
     /* 1 (default): skip, per block of voxels, the projections whose footprint
      * misses the detector (the line-wise clipping of Sect. 3.3 at block
      * granularity; the skipped terms are exactly zero, so the volume is
-     * bit-identical); 0: compute every term. */
+     * bit-identical); 0: compute every term.  For bp_adjoint, 1 also
+     * accumulates each block's footprint in shared memory before adding it
+     * to the images (fewer global atomics; same sums up to float32 order). */
     BP_OPT_CULL = 6
 } bp_option;
 

@@ -99,17 +99,177 @@ bp_adjoint_kernel(const __grid_constant__ AdjBatch b, const float *__restrict__ 
     }
 }
 
+// Shared-memory accumulation.  Per projection, 8 lanes of warp 0 project
+// the corners of the block's voxel box and the block agrees on its footprint
+// on the detector (clipped to it, with a pixel of margin).  Then
+//   * footprint off the detector: the projection is skipped (all of its
+//     terms would be dropped -- block culling, as in the forward kernel);
+//   * footprint of at most kAdjTile pixels: the block zeroes a tile of that
+//     size, scatters its 4 weighted corners per update with shared-memory
+//     atomics, and adds the tile's nonzero pixels to the image with one
+//     global atomic each (a few hundred per block instead of 4 per update);
+//   * larger footprint: global atomics per update, as in the direct kernel.
+// Same coordinates and weights as bp_adjoint_kernel.
+template <bool IEEE>
+__global__ void __launch_bounds__(kThreads)
+bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restrict__ vol, const VolGeom g,
+                       float *__restrict__ out, int isx, int isy)
+{
+    constexpr int LX = 8, LZ = 32 / LX, TX = LX * kVoxPerLane;
+    __shared__ float tile[kAdjTile];
+    // (x0, y0, W, H); W = 0 culled, W < 0 too large.  Two slots: warp 0
+    // writes the next projection's plan while slower warps may still read
+    // this one (a culled projection has no barrier after the read).
+    __shared__ int4 plan[2];
+    const int lane = threadIdx.x & 31;
+    const int tx = lane % LX, tz = lane / LX;
+    const int L = g.L;
+    const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * kWarpsY, bz0 = blockIdx.z * LZ;
+    const int xb = bx0 + tx;
+    const int y = by0 + (threadIdx.x >> 5);
+    const int z = bz0 + tz;
+    const bool live = y < L && z < L;
+
+    float f[kVoxPerLane], X[kVoxPerLane];
+#pragma unroll
+    for (int k = 0; k < kVoxPerLane; ++k) {
+        const int x = xb + LX * k;
+        f[k] = (live && x < L) ? vol[((size_t)z * L + y) * L + x] : 0.f;
+        X[k] = fmaf(g.R, (float)x, g.Ox);
+    }
+    const float Y = fmaf(g.R, (float)y, g.Oy);
+    const float Z = fmaf(g.R, (float)z, g.Oz);
+    // corner of the block's voxel box taken by lane c < 8 of warp 0
+    const int xe = min(bx0 + TX, L) - 1, ye = min(by0 + kWarpsY, L) - 1, ze = min(bz0 + LZ, L) - 1;
+    const float CX = fmaf(g.R, (float)((lane & 1) ? xe : bx0), g.Ox);
+    const float CY = fmaf(g.R, (float)((lane & 2) ? ye : by0), g.Oy);
+    const float CZ = fmaf(g.R, (float)((lane & 4) ? ze : bz0), g.Oz);
+
+#pragma unroll 1
+    for (int i = 0; i < b.n; ++i) {
+        const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+        const int2 kc = b.k[i];
+        if (threadIdx.x < 32) {
+            const float w = fmaf(rw.x, CX, fmaf(rw.y, CY, fmaf(rw.z, CZ, rw.w)));
+            const float r = 1.0f / w;
+            float umin = fmaf(ru.x, CX, fmaf(ru.y, CY, fmaf(ru.z, CZ, ru.w))) * r, umax = umin;
+            float vmin = fmaf(rv.x, CX, fmaf(rv.y, CY, fmaf(rv.z, CZ, rv.w))) * r, vmax = vmin;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+                umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+                vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+                vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            }
+            if (lane == 0) {
+                umin = fminf(fmaxf(umin, -1.0e6f), 1.0e6f);   // keep the int conversions in range
+                umax = fminf(fmaxf(umax, -1.0e6f), 1.0e6f);
+                vmin = fminf(fmaxf(vmin, -1.0e6f), 1.0e6f);
+                vmax = fminf(fmaxf(vmax, -1.0e6f), 1.0e6f);
+                // pixels touched: floor(u) .. floor(u) + 1 with u = u' + ku, one of margin
+                const int x0 = (int)floorf(umin) + kc.x - 1, x1 = (int)floorf(umax) + kc.x + 2;
+                const int y0 = (int)floorf(vmin) + kc.y - 1, y1 = (int)floorf(vmax) + kc.y + 2;
+                const int cx0 = max(x0, 0), cx1 = min(x1, isx - 1), cy0 = max(y0, 0), cy1 = min(y1, isy - 1);
+                int4 p = make_int4(cx0, cy0, 0, 0);
+                if (cx0 <= cx1 && cy0 <= cy1) {
+                    const int W = cx1 - cx0 + 1, H = cy1 - cy0 + 1;
+                    p.z = W * H <= kAdjTile ? W : -1;
+                    p.w = H;
+                }
+                plan[i & 1] = p;
+            }
+        }
+        __syncthreads();
+        const int4 p = plan[i & 1];
+        if (p.z == 0)
+            continue;   // the block's footprint misses the detector
+        float *img = out + b.out_off[i];
+        const bool tiled = p.z > 0;
+        if (tiled) {
+            for (int q = threadIdx.x; q < p.z * p.w; q += kThreads)
+                tile[q] = 0.f;
+            __syncthreads();
+        }
+        const float ulo = (float)(-1 - kc.x), uhi = (float)(isx - kc.x);
+        const float vlo = (float)(-1 - kc.y), vhi = (float)(isy - kc.y);
+        const float bu = fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w));
+        const float bv = fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w));
+        const float bw = fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w));
+#pragma unroll
+        for (int k = 0; k < kVoxPerLane; ++k) {
+            if (f[k] == 0.f)
+                continue;
+            const float uw = fmaf(ru.x, X[k], bu);
+            const float vw = fmaf(rv.x, X[k], bv);
+            const float w = fmaf(rw.x, X[k], bw);
+            const float r = recip_adj<IEEE>(w);
+            const float u = uw * r, v = vw * r;
+            if (!(u > ulo && u < uhi && v > vlo && v < vhi))
+                continue;
+            const float fu0 = floorf(u), fv0 = floorf(v);
+            const int iu = (int)fu0 + kc.x, iv = (int)fv0 + kc.y;
+            const float fu = u - fu0, fv = v - fv0;
+            const float s = f[k] * (r * r);
+            const float sb = s * fv, st = s - sb;
+            const float w_tr = st * fu, w_tl = st - w_tr;
+            const float w_br = sb * fu, w_bl = sb - w_br;
+            const bool in_l = iu >= 0, in_r = iu + 1 < isx, in_t = iv >= 0, in_b = iv + 1 < isy;
+            if (tiled) {
+                // index in the tile; the footprint box covers every in-detector
+                // corner, the unsigned clamp only guards the array
+                const int q0 = (iv - p.y) * p.z + (iu - p.x);
+                auto at = [&](int d) { return &tile[min((unsigned)(q0 + d), (unsigned)(kAdjTile - 1))]; };
+                if (in_t) {
+                    if (in_l) atomicAdd(at(0), w_tl);
+                    if (in_r) atomicAdd(at(1), w_tr);
+                }
+                if (in_b) {
+                    if (in_l) atomicAdd(at(p.z), w_bl);
+                    if (in_r) atomicAdd(at(p.z + 1), w_br);
+                }
+            } else {
+                const long long base = (long long)iv * isx + iu;
+                if (in_t) {
+                    if (in_l) atomicAdd(img + base, w_tl);
+                    if (in_r) atomicAdd(img + base + 1, w_tr);
+                }
+                if (in_b) {
+                    if (in_l) atomicAdd(img + base + isx, w_bl);
+                    if (in_r) atomicAdd(img + base + isx + 1, w_br);
+                }
+            }
+        }
+        if (tiled) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < p.z * p.w; q += kThreads) {
+                const float v = tile[q];
+                if (v != 0.f) {
+                    const int row = q / p.z, col = q - row * p.z;
+                    atomicAdd(img + (long long)(p.y + row) * isx + (p.x + col), v);
+                }
+            }
+        }
+        __syncthreads();   // tile and plan are reused by the next projection
+    }
+}
+
 cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom &g, float *out,
-                              int isx, int isy, bool ieee_rcp, cudaStream_t s)
+                              int isx, int isy, bool ieee_rcp, bool smem, cudaStream_t s)
 {
     if (b.n <= 0)
         return cudaSuccess;
     constexpr int TX = 8 * kVoxPerLane, LZ = 4;
     dim3 grid((g.L + TX - 1) / TX, (g.L + kWarpsY - 1) / kWarpsY, (g.L + LZ - 1) / LZ);
-    if (ieee_rcp)
+    if (smem) {
+        if (ieee_rcp)
+            bp_adjoint_smem_kernel<true><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
+        else
+            bp_adjoint_smem_kernel<false><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
+    } else if (ieee_rcp) {
         bp_adjoint_kernel<true><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
-    else
+    } else {
         bp_adjoint_kernel<false><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
+    }
     return cudaGetLastError();
 }
 

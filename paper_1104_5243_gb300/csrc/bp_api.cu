@@ -708,7 +708,7 @@ extern "C" bp_status bp_adjoint(bp_ctx *c, const float *vol, int vol_on_device, 
             b.k[j] = make_int2((int)ku, (int)kv);
             b.out_off[j] = (long long)(c0 + j) * (long long)img_elems;
         }
-        e = launch_bp_adjoint(b, dvol, g, dout, c->isx, c->isy, c->ieee_rcp, c->stream);
+        e = launch_bp_adjoint(b, dvol, g, dout, c->isx, c->isy, c->ieee_rcp, c->cull, c->stream);
     }
     if (e == cudaSuccess && !out_on_device) {
         e = cudaMemcpyAsync(images_out, dout, sizeof(float) * img_elems * n, cudaMemcpyDeviceToHost, c->stream);

@@ -69,8 +69,11 @@ long long fwd_blocks(int L, int lanes_x);
 cudaError_t launch_cull_masks(const FwdBatch &b, const VolGeom &g, int isx, int isy, int lanes_x,
                               unsigned long long *masks, unsigned long long *work, cudaStream_t s);
 
+// smem: accumulate each block's footprint in shared memory (kAdjTile pixels
+// at most) and add it to the image with one atomic per touched pixel.
+constexpr int kAdjTile = 3072;
 cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom &g,
-                              float *out, int isx, int isy, bool ieee_rcp, cudaStream_t s);
+                              float *out, int isx, int isy, bool ieee_rcp, bool smem, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // TMA / shared-memory path (bp_tma.cu).  Bricks of 16 x 8 x 8 voxels per

@@ -159,3 +159,27 @@ def test_gpu_fdk_chain_matches_oracle_chain():
         bp.add_projections(q, A)
         got = bp.finalize().cpu().numpy()
     assert rel_l2(got, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("L,scan", [
+    (32, synth.SCANS["grad"]),
+    (37, synth.Scan(n=70, isx=53, isy=41, pitch=384 / 53)),
+    (48, synth.Scan(n=20, isx=24, isy=10, pitch=4.0)),      # detector sees part of the volume
+])
+def test_shared_memory_adjoint_matches_direct_and_oracle(L, scan):
+    """The shared-memory adjoint (default) and the direct-atomic one give the
+    same images up to float32 summation order, and both match the oracle."""
+    api = native()
+    from paper_1104_5243_gb300 import _native as N
+    vol = synth.Volume(L)
+    A = oracle.carm_matrices(scan)
+    f = synth.uniform_volume(L, seed=L + 1) - 0.25
+    ref = oracle.adjoint(vol.L, vol.R, vol.O, f.astype(np.float64), A, scan.isx, scan.isy)
+    outs = []
+    for cull in (0, 1):
+        with make_bp(vol, scan) as bp:
+            bp.set_option(N.BP_OPT_CULL, cull)
+            outs.append(bp.adjoint(torch.from_numpy(f).cuda(), A).cpu().numpy())
+    assert rel_l2(outs[1], outs[0]) <= 1e-6
+    for o in outs:
+        assert rel_l2(o, ref) <= 1e-5
