@@ -87,7 +87,12 @@ typedef enum {
      * bit-identical); 0: compute every term.  For bp_adjoint, 1 also
      * accumulates each block's footprint in shared memory before adding it
      * to the images (fewer global atomics; same sums up to float32 order). */
-    BP_OPT_CULL = 6
+    BP_OPT_CULL = 6,
+    /* Host float32 images with the texture path: 1 (default) copy-engine
+     * transfers straight into the arrays, image by image; 0 one linear
+     * host-to-device copy per batch into a staging buffer, then a copy
+     * kernel into the arrays. */
+    BP_OPT_HOST_DIRECT = 7
 } bp_option;
 
 /* Queries for bp_query. */
@@ -229,7 +234,7 @@ bp_status bp_fdk_preweight(int n, int isx, int isy, double pitch, double sdd, do
 bp_status bp_ramp_filter(long long rows, int isx, double tau, const float *in, float *out,
                          void *stream);
 
-/* Short per-row filter (the learned replacement of the ramp, T <= 128 taps):
+/* Short per-row filter (the learned replacement of the ramp, T <= 256 taps):
  * out[r][j] = sum_t h[t] in[r][j + t - T/2], zero outside the row.
  * h: T float32 (device).  in and out must not overlap. */
 bp_status bp_row_filter_fwd(long long rows, int isx, int T, const float *h, const float *in,

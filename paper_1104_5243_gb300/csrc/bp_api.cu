@@ -78,6 +78,7 @@ struct bp_ctx {
     CUtensorMap maps[2][kMaxBatch];
     int *err_dev = nullptr;        // set by a kernel whose bounded wait gave up
     bool cull = true;              // BP_OPT_CULL
+    bool host_direct = true;       // BP_OPT_HOST_DIRECT (f32 host images: copy engine into arrays)
     unsigned long long *work_dev = nullptr;   // updates computed by culled launches
     unsigned long long work_host = 0;         // updates of launches without culling
     unsigned long long *masks = nullptr;   // per-block visibility masks (texture path)
@@ -272,6 +273,11 @@ extern "C" bp_status bp_set_option(bp_ctx *c, int option, long long value)
             return fail(c, BP_EINVAL, "bp_set_option: LANES_X takes 8, 16, 32, 44, 42, 82 or 24");
         c->lanes_x = (int)value;
         return BP_OK;
+    case BP_OPT_HOST_DIRECT:
+        if (value != 0 && value != 1)
+            return fail(c, BP_EINVAL, "bp_set_option: HOST_DIRECT takes 0 or 1");
+        c->host_direct = value != 0;
+        return BP_OK;
     case BP_OPT_CULL:
         if (value != 0 && value != 1)
             return fail(c, BP_EINVAL, "bp_set_option: CULL takes 0 or 1");
@@ -452,8 +458,8 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
         c->next_set ^= 1;
         CTX_CK(c, cudaStreamWaitEvent(c->copy_stream, c->kern_done[s], 0));
         const float *src0 = images + (size_t)c0 * img_elems;
-        if (!tma && c->dtype == BP_F32 && !images_on_device) {
-            // host images go straight into the arrays on the copy engine
+        if (!tma && c->dtype == BP_F32 && !images_on_device && c->host_direct) {
+            // host images straight into the arrays on the copy engine
             for (int j = 0; j < m; ++j)
                 CTX_CK(c, cudaMemcpy2DToArrayAsync(c->arr[s][j], 0, 0, src0 + (size_t)j * img_elems, row_bytes,
                                                    row_bytes, c->isy, cudaMemcpyHostToDevice, c->copy_stream));

@@ -285,7 +285,7 @@ ramp_kernel(long long rows, int isx, float tau, const float *__restrict__ in, fl
 // ---------------------------------------------------------------------------
 // Learned per-row filter.  kRowsPerBlock rows per block; each row sits in
 // shared memory with T zeros on the left and T on the right.
-constexpr int kMaxTaps = 128;
+constexpr int kMaxTaps = 256;
 constexpr int kRowsPerBlock = 4;
 
 __global__ void __launch_bounds__(256)

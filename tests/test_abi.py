@@ -72,7 +72,7 @@ def test_context_free_calls_validate_arguments(lib):
     assert lib.bp_ramp_filter(4, 0, 1.0, None, None, None) == N.BP_EINVAL
     assert lib.bp_ramp_filter(4, 16, -1.0, None, None, None) == N.BP_EINVAL
     assert lib.bp_row_filter_fwd(4, 16, 0, None, None, None, None) == N.BP_EINVAL
-    assert lib.bp_row_filter_fwd(4, 16, 129, None, None, None, None) == N.BP_EINVAL
+    assert lib.bp_row_filter_fwd(4, 16, 257, None, None, None, None) == N.BP_EINVAL
     assert lib.bp_carm_matrices(-1, None, 785.0, 1200.0, 1.0, 0.0, 0.0, None, None) == N.BP_EINVAL
     assert lib.bp_carm_matrices(3, None, 785.0, 1200.0, 1.0, 0.0, 0.0, None, None) == N.BP_EINVAL
     assert lib.bp_ellipsoid_project(1, None, 8, 8, 1000, None, None, None) == N.BP_EINVAL

@@ -81,3 +81,9 @@ def test_learned_filter_beats_ramp_fdk_on_heldout_phantoms():
           f"gain {res['mse_ramp'] / res['mse_learned']:.2f}x")
     assert res["mse_learned"] < 0.95 * res["mse_ramp"]
     assert all(a < b for a, b in zip(res["per_seed_learned"], res["per_seed_ramp"]))
+    # inference at the full size: 512^3 x 496 x 1248x960, the learned change
+    # resampled to the 4x finer detector, the same dose per mm^2
+    full = lm.full_size_inference(filt, [9000])
+    print(f"full-size MSE learned {full['mse_learned']:.4e} ramp {full['mse_ramp']:.4e} "
+          f"({full['taps']} taps, {full['photons_per_pixel']:.0f} photons per pixel)")
+    assert full["mse_learned"] <= full["mse_ramp"]
