@@ -72,7 +72,9 @@ typedef enum {
     BP_OPT_TIMING = 3,
     /* Warp layout of the backprojection kernel: 8, 16 or 32 lanes along x
      * (the rest along z), or a two-digit code XY = X lanes along x by Y along
-     * y (44, 42, 82, 24; the rest along z).  Default 8.  Changes speed only:
+     * y (44, 42, 82, 24; the rest along z), or 108 (8 lanes along x, 8
+     * voxels per lane instead of 4).  Default 8 for BP_F32 projections and
+     * 108 for BP_F16 / BP_BF16 (fastest on GB300).  Changes speed only:
      * every voxel still sums its projections in the same order. */
     BP_OPT_LANES_X = 4,
     /* Data path of the backprojection: 0 (default) automatic, 1 texture

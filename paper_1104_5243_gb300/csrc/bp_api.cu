@@ -198,6 +198,10 @@ extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
     c->isx = isx;
     c->isy = isy;
     c->dtype = proj_dtype;
+    // default warp layout: 4 voxels per lane for float32 projections (gather
+    // bound), 8 for 16-bit ones (closer to the issue bound, where halving the
+    // per-projection overhead per update pays)
+    c->lanes_x = proj_dtype == BP_F32 ? 8 : 108;
     bp_status st = BP_OK;
     auto check = [&](cudaError_t e, const char *what) {
         if (st == BP_OK && e != cudaSuccess)
@@ -269,8 +273,9 @@ extern "C" bp_status bp_set_option(bp_ctx *c, int option, long long value)
         c->batch = (int)value;
         return BP_OK;
     case BP_OPT_LANES_X:
-        if (value != 8 && value != 16 && value != 32 && value != 44 && value != 42 && value != 82 && value != 24)
-            return fail(c, BP_EINVAL, "bp_set_option: LANES_X takes 8, 16, 32, 44, 42, 82 or 24");
+        if (value != 8 && value != 16 && value != 32 && value != 44 && value != 42 && value != 82 && value != 24 &&
+            value != 108)
+            return fail(c, BP_EINVAL, "bp_set_option: LANES_X takes 8, 16, 32, 44, 42, 82, 24 or 108");
         c->lanes_x = (int)value;
         return BP_OK;
     case BP_OPT_HOST_DIRECT:

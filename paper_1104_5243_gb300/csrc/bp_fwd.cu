@@ -67,13 +67,13 @@ __device__ __forceinline__ float4 gather(cudaTextureObject_t t, float x, float y
     }
 }
 
-template <int KIND, bool IEEE, int LX, int LY>
-__global__ void __launch_bounds__(kThreads, 6)
+template <int KIND, bool IEEE, int LX, int LY, int VPL>
+__global__ void __launch_bounds__(kThreads, VPL == 4 ? 6 : 4)
 bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const VolGeom g,
               int accumulate, const unsigned long long *__restrict__ masks)
 {
     constexpr int LZ = 32 / (LX * LY);          // lanes along z
-    constexpr int TX = LX * kVoxPerLane;        // x extent of the block tile
+    constexpr int TX = LX * VPL;                // x extent of the block tile
     const int lane = threadIdx.x & 31;
     const int tx = lane % LX, ty = (lane / LX) % LY, tz = lane / (LX * LY);
     const int L = g.L;
@@ -83,16 +83,16 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
     if (y >= L || z >= L)
         return;
 
-    float X[kVoxPerLane];
+    float X[VPL];
 #pragma unroll
-    for (int k = 0; k < kVoxPerLane; ++k)
+    for (int k = 0; k < VPL; ++k)
         X[k] = fmaf(g.R, (float)(xb + LX * k), g.Ox);
     const float Y = fmaf(g.R, (float)y, g.Oy);
     const float Z = fmaf(g.R, (float)z, g.Oz);
 
-    float acc[kVoxPerLane];
+    float acc[VPL];
 #pragma unroll
-    for (int k = 0; k < kVoxPerLane; ++k)
+    for (int k = 0; k < VPL; ++k)
         acc[k] = 0.f;
     // projections that can reach this block (all of them without culling)
     const unsigned long long visible =
@@ -109,7 +109,7 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
         const float bv = fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w));
         const float bw = fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w));
 #pragma unroll
-        for (int k = 0; k < kVoxPerLane; ++k) {
+        for (int k = 0; k < VPL; ++k) {
             const float uw = fmaf(ru.x, X[k], bu);
             const float vw = fmaf(rv.x, X[k], bv);
             const float w = fmaf(rw.x, X[k], bw);
@@ -129,7 +129,7 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
 
     float *row = vol + ((size_t)z * L + y) * L;
 #pragma unroll
-    for (int k = 0; k < kVoxPerLane; ++k) {
+    for (int k = 0; k < VPL; ++k) {
         const int x = xb + LX * k;
         if (x < L)
             row[x] = (accumulate ? row[x] : 0.f) + acc[k];
@@ -139,8 +139,9 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
 // Block tile of a layout: (TX, TY, TZ) voxels.
 static void layout_tile(int lanes_x, int *tx, int *ty, int *tz)
 {
-    int lx = 8, ly = 1;
+    int lx = 8, ly = 1, vpl = kVoxPerLane;
     switch (lanes_x) {
+    case 108: vpl = 8; break;
     case 32: lx = 32; break;
     case 16: lx = 16; break;
     case 44: lx = 4; ly = 4; break;
@@ -149,7 +150,7 @@ static void layout_tile(int lanes_x, int *tx, int *ty, int *tz)
     case 24: lx = 2; ly = 4; break;
     default: break;
     }
-    *tx = lx * kVoxPerLane;
+    *tx = lx * vpl;
     *ty = kWarpsY * ly;
     *tz = 32 / (lx * ly);
 }
@@ -161,13 +162,13 @@ long long fwd_blocks(int L, int lanes_x)
     return (long long)((L + tx - 1) / tx) * ((L + ty - 1) / ty) * ((L + tz - 1) / tz);
 }
 
-template <int KIND, bool IEEE, int LX, int LY>
+template <int KIND, bool IEEE, int LX, int LY, int VPL = kVoxPerLane>
 static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bool acc,
                              const unsigned long long *masks, cudaStream_t s)
 {
-    constexpr int TX = LX * kVoxPerLane, TY = kWarpsY * LY, LZ = 32 / (LX * LY);
+    constexpr int TX = LX * VPL, TY = kWarpsY * LY, LZ = 32 / (LX * LY);
     dim3 grid((g.L + TX - 1) / TX, (g.L + TY - 1) / TY, (g.L + LZ - 1) / LZ);
-    bp_fwd_kernel<KIND, IEEE, LX, LY><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0, masks);
+    bp_fwd_kernel<KIND, IEEE, LX, LY, VPL><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0, masks);
     return cudaGetLastError();
 }
 
@@ -245,7 +246,8 @@ cudaError_t launch_cull_masks(const FwdBatch &b, const VolGeom &g, int isx, int 
 
 // Warp layouts (bp_set_option BP_OPT_LANES_X): 8, 16, 32 = lanes along x
 // (the rest along z); two-digit codes XY = X lanes along x by Y along y
-// (the rest along z): 44, 42, 82, 24.
+// (the rest along z): 44, 42, 82, 24; 108 = 8 lanes along x with 8 voxels
+// per lane (instead of 4).
 template <int KIND, bool IEEE>
 static cudaError_t launch_kind(const FwdBatch &b, float *vol, const VolGeom &g, bool acc, int layout,
                                const unsigned long long *m, cudaStream_t s)
@@ -257,6 +259,7 @@ static cudaError_t launch_kind(const FwdBatch &b, float *vol, const VolGeom &g, 
     case 42: return launch_lx<KIND, IEEE, 4, 2>(b, vol, g, acc, m, s);
     case 82: return launch_lx<KIND, IEEE, 8, 2>(b, vol, g, acc, m, s);
     case 24: return launch_lx<KIND, IEEE, 2, 4>(b, vol, g, acc, m, s);
+    case 108: return launch_lx<KIND, IEEE, 8, 1, 8>(b, vol, g, acc, m, s);
     default: return launch_lx<KIND, IEEE, 8, 1>(b, vol, g, acc, m, s);
     }
 }

@@ -15,7 +15,8 @@ data set is not available, so seeded synthetic stacks stand in for it:
 * timing stack: uniform [0, 1) float32 projections (PCG64 seed 20110426);
 * phantoms: random ellipsoids with densities U[0.1, 1] (scaled by 0.02/mm so
   line integrals are water-like), semi-axes U[8, 64] mm, uniform random
-  orientation, centres inside 0.8 x the field-of-view cylinder.
+  orientation, centres inside 0.8 x the field-of-view cylinder (clipped to
+  the 256 mm cube).
 """
 from __future__ import annotations
 
@@ -116,6 +117,9 @@ def ellipsoids(count: int, seed: int, scan: Scan) -> np.ndarray:
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     radius, half_h = field_of_view(scan)
+    # centres inside the field of view and inside the reconstructed cube
+    radius = min(radius, VOLUME_MM / 2)
+    half_h = min(half_h, VOLUME_MM / 2)
     out = np.zeros((count, 16), dtype=np.float64)
     for e in range(count):
         rr = 0.8 * radius * math.sqrt(rng.random())

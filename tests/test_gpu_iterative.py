@@ -13,29 +13,54 @@ from gpu_common import native, rel_l2, torch
 pytestmark = pytest.mark.gpu
 
 
-def test_cgls_converges_to_dense_least_squares_solution():
+def dense_cgls(P, p, iters):
+    """The same CGLS recurrence in float64 on an explicit matrix."""
+    f = np.zeros(P.shape[1])
+    r = p.copy()
+    s = P.T @ r
+    d = s.copy()
+    gamma = s @ s
+    for _ in range(iters):
+        q = P @ d
+        alpha = gamma / (q @ q)
+        f += alpha * d
+        r -= alpha * q
+        s = P.T @ r
+        gamma_new = s @ s
+        d = s + (gamma_new / gamma) * d
+        gamma = gamma_new
+    return f
+
+
+def test_cgls_iterates_match_float64_cgls_on_the_oracle_matrix():
+    """The GPU iterates after k steps equal those of CGLS in float64 on the
+    system matrix built column by column from the oracle's adjoint."""
     native()
     from paper_1104_5243_gb300 import api, iterative
     scan, vol = synth.Scan(n=8, isx=24, isy=18, pitch=16.0), synth.Volume(8)
     A = oracle.carm_matrices(scan)
     n_vox = vol.L ** 3
-    # dense forward matrix from the oracle's adjoint of unit voxels
     P = np.zeros((scan.n * scan.isy * scan.isx, n_vox))
     for j in range(n_vox):
         e = np.zeros(n_vox)
         e[j] = 1.0
         P[:, j] = oracle.adjoint(vol.L, vol.R, vol.O, e.reshape((vol.L,) * 3), A, scan.isx, scan.isy).ravel()
     rng = np.random.default_rng(0)
-    f_true = rng.random(n_vox)
-    p = P @ f_true + 1e-3 * rng.standard_normal(P.shape[0])
-    f_ls = np.linalg.lstsq(P, p, rcond=None)[0]
+    p = P @ rng.random(n_vox) + 1e-3 * rng.standard_normal(P.shape[0])
     bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
     ops = iterative.Operators(bp, A, scale=1.0)
     pt = torch.from_numpy(p.reshape(scan.n, scan.isy, scan.isx).astype(np.float32)).cuda()
-    f, norms = iterative.cgls(ops, pt, iters=150)
+    for k in (1, 5, 12):
+        f, norms = iterative.cgls(ops, pt, iters=k)
+        assert rel_l2(f.cpu().numpy().ravel(), dense_cgls(P, p, k)) <= 1e-3 * k
+    f, norms = iterative.cgls(ops, pt, iters=60)
     bp.close()
-    assert all(b <= a * (1 + 1e-4) for a, b in zip(norms, norms[1:]))   # CGLS: residual never grows
-    assert rel_l2(f.cpu().numpy().ravel(), f_ls) <= 2e-3
+    assert all(b <= a * (1 + 1e-4) for a, b in zip(norms, norms[1:]))   # CGLS: the residual never grows
+    # heading for the least-squares residual (this small system is badly
+    # conditioned, so 60 steps get within a factor 2, not to it)
+    f_ls = np.linalg.lstsq(P, p, rcond=None)[0]
+    r_ls = np.linalg.norm(P @ f_ls - p)
+    assert r_ls <= norms[-1] <= 2.0 * r_ls and norms[-1] < 0.01 * norms[0]
 
 
 def test_cgls_improves_on_the_phantom_and_reduces_the_residual():
@@ -44,6 +69,8 @@ def test_cgls_improves_on_the_phantom_and_reduces_the_residual():
     scan, vol = synth.SCANS["tiny"], synth.Volume(64)
     A = oracle.carm_matrices(scan)
     ell = synth.ellipsoids(10, seed=1, scan=scan)
+    ell[:, 0:3] *= 0.5   # keep the ellipsoids well inside the reconstructed cube
+    ell[:, 3:6] *= 0.5
     lines = api.ellipsoid_project(A, scan.isx, scan.isy, ell)
     target = api.ellipsoid_voxelize(vol.L, vol.R, vol.O, ell)
     bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
