@@ -444,9 +444,10 @@ def main():
         "roofline": roofline,
         "clocks": clocks,
         "e2e": e2e,
-        # backprojection kernels, plus one FP32->16-bit conversion kernel per
-        # batch for the 16-bit forms
-        "gpu_launches": sum(v["launches"] * (1 if kk == "f32" else 2) for kk, v in kernel.items()),
+        # per batch of 64 projections: the copy/conversion kernel into the
+        # projection arrays, the block pre-pass (culling masks; centring
+        # records for FP32) and the backprojection kernel
+        "gpu_launches": sum(v["launches"] * 3 for kk, v in kernel.items()),
         "cpu_baseline": cpu,
         "paths": {kk: path_taken.get(kk) for kk in forms},
         **extra,

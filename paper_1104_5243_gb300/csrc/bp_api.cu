@@ -81,8 +81,13 @@ struct bp_ctx {
     bool host_direct = true;       // BP_OPT_HOST_DIRECT (f32 host images: copy engine into arrays)
     unsigned long long *work_dev = nullptr;   // updates computed by culled launches
     unsigned long long work_host = 0;         // updates of launches without culling
-    unsigned long long *masks = nullptr;   // per-block visibility masks (texture path)
-    long long mask_blocks = 0;
+    // texture path, per input set: per-block visibility masks and
+    // per-(block, projection) centring records, built on the copy stream
+    unsigned long long *masks[2] = {nullptr, nullptr};
+    long long mask_blocks[2] = {0, 0};
+    bool block_centre = true;      // BP_OPT_BLOCK_CENTRE (float32 projections)
+    float4 *centres[2] = {nullptr, nullptr};
+    long long centre_blocks[2] = {0, 0};
     size_t ev_used = 0;
     char err[1024] = "no error";
 };
@@ -140,8 +145,12 @@ static void release(bp_ctx *c)
         cudaFree(c->vol);
     if (c->err_dev)
         cudaFree(c->err_dev);
-    if (c->masks)
-        cudaFree(c->masks);
+    for (int s = 0; s < 2; ++s) {
+        if (c->masks[s])
+            cudaFree(c->masks[s]);
+        if (c->centres[s])
+            cudaFree(c->centres[s]);
+    }
     if (c->work_dev)
         cudaFree(c->work_dev);
     if (c->copy_stream)
@@ -282,6 +291,11 @@ extern "C" bp_status bp_set_option(bp_ctx *c, int option, long long value)
         if (value != 0 && value != 1)
             return fail(c, BP_EINVAL, "bp_set_option: HOST_DIRECT takes 0 or 1");
         c->host_direct = value != 0;
+        return BP_OK;
+    case BP_OPT_BLOCK_CENTRE:
+        if (value != 0 && value != 1)
+            return fail(c, BP_EINVAL, "bp_set_option: BLOCK_CENTRE takes 0 or 1");
+        c->block_centre = value != 0;
         return BP_OK;
     case BP_OPT_CULL:
         if (value != 0 && value != 1)
@@ -496,6 +510,63 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 CTX_CK(c, launch_convert(cb, c->isx, c->isy, mode, c->copy_stream));
             }
         }
+        // Texture path: the batch's kernel parameters, and the per-block
+        // pre-pass (culling masks, centring records) on the copy stream: it
+        // needs only the matrices, so it overlaps the previous batch's
+        // backprojection; its buffers belong to this input set, which the
+        // copy stream has waited for.
+        FwdBatch b;
+        unsigned long long *masks = nullptr;
+        float4 *centres = nullptr;
+        if (!tma) {
+            b.n = m;
+            double rows[kMaxBatch][3][4];   // the same centred rows in float64
+            for (int j = 0; j < m; ++j) {
+                const double *a = A0 + 12 * (size_t)j;
+                // u' = u - ku + 1 = (uw - (ku - 1) w) / w; gather at floor(u') + ku
+                double ku, kv;
+                centre_offsets(c, a, &ku, &kv);
+                b.m[j][0] = row4(a, 0, 1.0 - ku);
+                b.m[j][1] = row4(a, 1, 1.0 - kv);
+                b.m[j][2] = row4(a, 2, 0.0);
+                b.k[j] = make_float2((float)ku, (float)kv);
+                b.tex[j] = c->tex[s][j];
+                for (int q = 0; q < 4; ++q) {
+                    rows[j][0][q] = a[q] + (1.0 - ku) * a[8 + q];
+                    rows[j][1][q] = a[4 + q] + (1.0 - kv) * a[8 + q];
+                    rows[j][2][q] = a[8 + q];
+                }
+            }
+            const long long nb = fwd_blocks(c->L, c->lanes_x);
+            if (c->cull) {
+                if (nb > c->mask_blocks[s]) {
+                    if (c->masks[s])
+                        CTX_CK(c, cudaFree(c->masks[s]));
+                    c->masks[s] = nullptr;
+                    c->mask_blocks[s] = 0;
+                    CTX_CK(c, cudaMalloc((void **)&c->masks[s], sizeof(unsigned long long) * nb));
+                    c->mask_blocks[s] = nb;
+                }
+                masks = c->masks[s];
+            } else {
+                c->work_host += (unsigned long long)m * c->L * c->L * c->L;
+            }
+            CentreBatch cb;
+            if (c->dtype == BP_F32 && c->block_centre) {
+                if (nb > c->centre_blocks[s]) {
+                    if (c->centres[s])
+                        CTX_CK(c, cudaFree(c->centres[s]));
+                    c->centres[s] = nullptr;
+                    c->centre_blocks[s] = 0;
+                    CTX_CK(c, cudaMalloc((void **)&c->centres[s], sizeof(float4) * kMaxBatch * nb));
+                    c->centre_blocks[s] = nb;
+                }
+                centres = c->centres[s];
+                centre_batch(&cb, &rows[0][0][0], m, c->O, c->R);
+            }
+            CTX_CK(c, launch_block_prepass(b, centres ? &cb : nullptr, g, c->isx, c->isy, c->lanes_x, masks, centres,
+                                           masks ? c->work_dev : nullptr, c->copy_stream));
+        }
         CTX_CK(c, cudaEventRecord(c->copy_done[s], c->copy_stream));
         CTX_CK(c, cudaStreamWaitEvent(c->stream, c->copy_done[s], 0));
         cudaEvent_t ev_stop;
@@ -522,37 +593,8 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
             CTX_CK(c, launch_bp_tma(tb, c->vol, g, pair_kind(c), !c->vol_zero, c->ieee_rcp, c->err_dev, c->work_dev,
                                     c->stream));
         } else {
-            FwdBatch b;
-            b.n = m;
-            for (int j = 0; j < m; ++j) {
-                const double *a = A0 + 12 * (size_t)j;
-                // u' = u - ku + 1 = (uw - (ku - 1) w) / w; gather at floor(u') + ku
-                double ku, kv;
-                centre_offsets(c, a, &ku, &kv);
-                b.m[j][0] = row4(a, 0, 1.0 - ku);
-                b.m[j][1] = row4(a, 1, 1.0 - kv);
-                b.m[j][2] = row4(a, 2, 0.0);
-                b.k[j] = make_float2((float)ku, (float)kv);
-                b.tex[j] = c->tex[s][j];
-            }
-            unsigned long long *masks = nullptr;
-            if (c->cull) {
-                const long long nb = fwd_blocks(c->L, c->lanes_x);
-                if (nb > c->mask_blocks) {
-                    if (c->masks)
-                        CTX_CK(c, cudaFree(c->masks));
-                    c->masks = nullptr;
-                    c->mask_blocks = 0;
-                    CTX_CK(c, cudaMalloc((void **)&c->masks, sizeof(unsigned long long) * nb));
-                    c->mask_blocks = nb;
-                }
-                masks = c->masks;
-                CTX_CK(c, launch_cull_masks(b, g, c->isx, c->isy, c->lanes_x, masks, c->work_dev, c->stream));
-            } else {
-                c->work_host += (unsigned long long)m * c->L * c->L * c->L;
-            }
             CTX_CK(c, launch_bp_fwd(b, c->vol, g, c->dtype == BP_BF16 ? kTexBF16 : kTexFloat, !c->vol_zero,
-                                    c->ieee_rcp, c->lanes_x, masks, c->stream));
+                                    c->ieee_rcp, c->lanes_x, masks, centres, c->stream));
         }
         if (ev_stop)
             CTX_CK(c, cudaEventRecord(ev_stop, c->stream));

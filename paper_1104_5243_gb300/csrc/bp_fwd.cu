@@ -33,6 +33,12 @@
 //    footprint can reach the block's voxels; the others are skipped with a
 //    block-uniform branch.  Skipped terms are exactly zero, so culling does
 //    not change a single bit of the volume.
+//  * Per-block centring (float32 form): the same pre-pass gives every
+//    (block, projection) integer offsets near the block centre's projection
+//    and the centred homogeneous values there, exact to float-float
+//    precision.  The kernel adds offsets from the block centre, so u' and v'
+//    stay within the block's footprint (tens of pixels) instead of the
+//    volume's, and their float32 rounding shrinks accordingly.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -67,51 +73,81 @@ __device__ __forceinline__ float4 gather(cudaTextureObject_t t, float x, float y
     }
 }
 
-template <int KIND, bool IEEE, int LX, int LY, int VPL>
+template <int KIND, bool IEEE, int LX, int LY, int VPL, bool BLK>
 __global__ void __launch_bounds__(kThreads, VPL == 4 ? 6 : 4)
 bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const VolGeom g,
-              int accumulate, const unsigned long long *__restrict__ masks)
+              int accumulate, const unsigned long long *__restrict__ masks,
+              const float4 *__restrict__ centres)
 {
     constexpr int LZ = 32 / (LX * LY);          // lanes along z
     constexpr int TX = LX * VPL;                // x extent of the block tile
+    constexpr int TY = kWarpsY * LY;
     const int lane = threadIdx.x & 31;
     const int tx = lane % LX, ty = (lane / LX) % LY, tz = lane / (LX * LY);
     const int L = g.L;
     const int xb = blockIdx.x * TX + tx;        // this lane's voxels: xb + LX k
-    const int y = (blockIdx.y * kWarpsY + (threadIdx.x >> 5)) * LY + ty;
+    const int y = blockIdx.y * TY + (threadIdx.x >> 5) * LY + ty;
     const int z = blockIdx.z * LZ + tz;
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    // BLK: the block's centring records, one per projection, staged once
+    __shared__ float4 cen[BLK ? kMaxBatch : 1];
+    if constexpr (BLK) {
+        if (threadIdx.x < b.n)
+            cen[threadIdx.x] = centres[(size_t)threadIdx.x * gridDim.x * gridDim.y * gridDim.z + blk];
+        __syncthreads();
+    }
     if (y >= L || z >= L)
         return;
 
-    float X[VPL];
+    // absolute voxel coordinates (the w row), and with BLK the offsets from
+    // the centre of the block's voxel box clipped to the volume (the u and v
+    // rows); the centre index (x0 + x1) / 2 is a multiple of 1/2, so the
+    // offsets are exact before the product with R
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * LZ;
+    const float hx = 0.5f * (float)(x0 + min(x0 + TX, L) - 1);
+    const float hy = 0.5f * (float)(y0 + min(y0 + TY, L) - 1);
+    const float hz = 0.5f * (float)(z0 + min(z0 + LZ, L) - 1);
+    float X[VPL], dX[VPL];
 #pragma unroll
-    for (int k = 0; k < VPL; ++k)
+    for (int k = 0; k < VPL; ++k) {
         X[k] = fmaf(g.R, (float)(xb + LX * k), g.Ox);
+        dX[k] = BLK ? g.R * ((float)(xb + LX * k) - hx) : X[k];
+    }
     const float Y = fmaf(g.R, (float)y, g.Oy);
     const float Z = fmaf(g.R, (float)z, g.Oz);
+    const float dY = BLK ? g.R * ((float)y - hy) : Y;
+    const float dZ = BLK ? g.R * ((float)z - hz) : Z;
 
     float acc[VPL];
 #pragma unroll
     for (int k = 0; k < VPL; ++k)
         acc[k] = 0.f;
     // projections that can reach this block (all of them without culling)
-    const unsigned long long visible =
-        masks ? masks[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] : ~0ull;
+    const unsigned long long visible = masks ? masks[blk] : ~0ull;
 #pragma unroll 1
     for (int i = 0; i < b.n; ++i) {
         if (!((visible >> i) & 1ull))
             continue;   // every term of this projection is exactly zero here
-        const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
-        const float2 kc = b.k[i];
+        float4 ru = b.m[i][0], rv = b.m[i][1];
+        const float4 rw = b.m[i][2];
+        float2 kc = b.k[i];
         const cudaTextureObject_t t = b.tex[i];
+        if constexpr (BLK) {
+            // recentre on (ku + dku, kv + dkv): row_u'' = row_u' - dku row_w,
+            // whose value at the block centre is c.x
+            const float4 c = cen[i];
+            ru = make_float4(fmaf(-c.z, rw.x, ru.x), fmaf(-c.z, rw.y, ru.y), fmaf(-c.z, rw.z, ru.z), c.x);
+            rv = make_float4(fmaf(-c.w, rw.x, rv.x), fmaf(-c.w, rw.y, rv.y), fmaf(-c.w, rw.z, rv.z), c.y);
+            kc = make_float2(kc.x + c.z, kc.y + c.w);
+        }
         // Part 1: geometry; the y, z terms are shared by the lane's voxels.
-        const float bu = fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w));
-        const float bv = fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w));
+        const float bu = fmaf(ru.y, dY, fmaf(ru.z, dZ, ru.w));
+        const float bv = fmaf(rv.y, dY, fmaf(rv.z, dZ, rv.w));
         const float bw = fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w));
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
-            const float uw = fmaf(ru.x, X[k], bu);
-            const float vw = fmaf(rv.x, X[k], bv);
+            const float uw = fmaf(ru.x, dX[k], bu);
+            const float vw = fmaf(rv.x, dX[k], bv);
             const float w = fmaf(rw.x, X[k], bw);
             const float r = recip<IEEE>(w);
             const float u = uw * r, v = vw * r;       // centred: u - ku + 1
@@ -164,84 +200,193 @@ long long fwd_blocks(int L, int lanes_x)
 
 template <int KIND, bool IEEE, int LX, int LY, int VPL = kVoxPerLane>
 static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bool acc,
-                             const unsigned long long *masks, cudaStream_t s)
+                             const unsigned long long *masks, const float4 *centres, cudaStream_t s)
 {
     constexpr int TX = LX * VPL, TY = kWarpsY * LY, LZ = 32 / (LX * LY);
     dim3 grid((g.L + TX - 1) / TX, (g.L + TY - 1) / TY, (g.L + LZ - 1) / LZ);
-    bp_fwd_kernel<KIND, IEEE, LX, LY, VPL><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0, masks);
+    if constexpr (KIND == kTexFloat) {
+        if (centres) {
+            bp_fwd_kernel<KIND, IEEE, LX, LY, VPL, true><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0, masks,
+                                                                                    centres);
+            return cudaGetLastError();
+        }
+    }
+    bp_fwd_kernel<KIND, IEEE, LX, LY, VPL, false><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0, masks, nullptr);
     return cudaGetLastError();
 }
 
-// Visibility mask of one thread block of the texture kernel: project the 8
-// corners of the block's voxel box (clamped to the volume) for every
-// projection of the batch, with the kernel's float32 arithmetic, and keep
-// the projection when the footprint, widened by one pixel, touches
-// [-1, isx] x [-1, isy].  Returns the number of voxel updates it keeps.
-__device__ unsigned long long block_mask(const FwdBatch &b, const VolGeom &g, int isx, int isy, int x0, int y0,
-                                         int z0, int x1, int y1, int z1, unsigned long long *mask)
+// Float-float arithmetic (Dekker, Knuth): a value is the unevaluated sum
+// hi + lo of two float32 numbers.  The explicit _rn intrinsics keep the
+// compiler from contracting the error terms into FMAs.
+struct Ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ Ff two_sum(float a, float b)
 {
-    unsigned long long m = 0;
-    for (int i = 0; i < b.n; ++i) {
-        const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
-        float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float X = fmaf(g.R, (float)((c & 1) ? x1 : x0), g.Ox);
-            const float Y = fmaf(g.R, (float)((c & 2) ? y1 : y0), g.Oy);
-            const float Z = fmaf(g.R, (float)((c & 4) ? z1 : z0), g.Oz);
-            const float w = fmaf(rw.x, X, fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w)));
-            const float r = 1.0f / w;
-            const float u = fmaf(ru.x, X, fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w))) * r;
-            const float v = fmaf(rv.x, X, fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w))) * r;
-            umin = fminf(umin, u);
-            umax = fmaxf(umax, u);
-            vmin = fminf(vmin, v);
-            vmax = fmaxf(vmax, v);
-        }
-        // centred coordinates: pixel u = u' + ku - 1; keep unless the box,
-        // widened by a pixel, lies entirely left of -1 or right of isx
-        const float2 kc = b.k[i];
-        const float pu0 = umin + kc.x - 2.f, pu1 = umax + kc.x;
-        const float pv0 = vmin + kc.y - 2.f, pv1 = vmax + kc.y;
-        const bool miss = pu1 < -1.f || pu0 > (float)isx || pv1 < -1.f || pv0 > (float)isy;
-        if (!miss)
-            m |= 1ull << i;
-    }
-    *mask = m;
-    return (unsigned long long)__popcll(m) * (x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1);
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
 }
 
-// One thread per block of the texture kernel; the kept updates are summed
-// per warp into the context's work counter (for the roofline).
+__device__ __forceinline__ Ff ff_norm(float hi, float lo)   // needs |hi| >= |lo| or hi == 0
+{
+    const float s = __fadd_rn(hi, lo);
+    return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+
+__device__ __forceinline__ Ff ff_add(Ff a, Ff b)
+{
+    const Ff s = two_sum(a.hi, b.hi);
+    return ff_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+// a * n for an integer-valued float n (|n| < 2^24): the product of the high
+// parts is split exactly with an FMA.
+__device__ __forceinline__ Ff ff_mul_int(Ff a, float n)
+{
+    const float p = __fmul_rn(a.hi, n);
+    const float e = fmaf(a.lo, n, fmaf(a.hi, n, -p));
+    return ff_norm(p, e);
+}
+
+// Footprint test of one (block, projection): project the 8 corners of the
+// block's voxel box (clamped to the volume) with float32 arithmetic and keep
+// the projection when the footprint, widened by one pixel, touches
+// [-1, isx] x [-1, isy].  The kernel's coordinates differ from these by far
+// less than the pixel of margin.
+__device__ bool footprint_hits(const FwdBatch &b, int i, const VolGeom &g, int isx, int isy, int x0, int y0,
+                               int z0, int x1, int y1, int z1)
+{
+    const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float X = fmaf(g.R, (float)((c & 1) ? x1 : x0), g.Ox);
+        const float Y = fmaf(g.R, (float)((c & 2) ? y1 : y0), g.Oy);
+        const float Z = fmaf(g.R, (float)((c & 4) ? z1 : z0), g.Oz);
+        const float w = fmaf(rw.x, X, fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w)));
+        const float r = 1.0f / w;
+        const float u = fmaf(ru.x, X, fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w))) * r;
+        const float v = fmaf(rv.x, X, fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w))) * r;
+        umin = fminf(umin, u);
+        umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v);
+        vmax = fmaxf(vmax, v);
+    }
+    // centred coordinates: pixel u = u' + ku - 1; keep unless the box,
+    // widened by a pixel, lies entirely left of -1 or right of isx
+    const float2 kc = b.k[i];
+    const float pu0 = umin + kc.x - 2.f, pu1 = umax + kc.x;
+    const float pv0 = vmin + kc.y - 2.f, pv1 = vmax + kc.y;
+    return !(pu1 < -1.f || pu0 > (float)isx || pv1 < -1.f || pv0 > (float)isy);
+}
+
+// Centring record of the block whose clipped voxel box has its centre at
+// voxel index (cx2, cy2, cz2) / 2, for projection i: the rows' values there
+// as float-float sums C + cx2 Hx + cy2 Hy + cz2 Hz, the offsets
+// dku = round(u'_c), dkv = round(v'_c), and the recentred values
+// uw_c - dku w_c, vw_c - dkv w_c rounded to float32 once.  The centre lies
+// in the volume, where the host has checked w > 0.
+__device__ float4 block_centre(const CentreBatch &cb, int i, int cx2, int cy2, int cz2)
+{
+    Ff val[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float2 *c = cb.c[i][r];
+        const Ff sx = ff_mul_int({c[1].x, c[1].y}, (float)cx2);
+        const Ff sy = ff_mul_int({c[2].x, c[2].y}, (float)cy2);
+        const Ff sz = ff_mul_int({c[3].x, c[3].y}, (float)cz2);
+        val[r] = ff_add(ff_add({c[0].x, c[0].y}, sx), ff_add(sy, sz));
+    }
+    float dku = rintf(val[0].hi / val[2].hi), dkv = rintf(val[1].hi / val[2].hi);
+    // any integer is a valid offset; keep them exact and finite
+    if (!(fabsf(dku) <= 1048576.f))
+        dku = 0.f;
+    if (!(fabsf(dkv) <= 1048576.f))
+        dkv = 0.f;
+    const Ff du = ff_mul_int(val[2], -dku), dv = ff_mul_int(val[2], -dkv);
+    return make_float4(ff_add(val[0], du).hi, ff_add(val[1], dv).hi, dku, dkv);
+}
+
+// One thread per block of the texture kernel, looping over the projections
+// of the batch (a warp-uniform index: the matrices are read from kernel
+// parameter space by broadcast).  Records are stored projection-major,
+// centres[i * nblocks + block], so a warp's stores are contiguous.  The kept
+// updates are summed per warp into the context's work counter (for the
+// roofline).
+template <bool CENTRES>
 __global__ void __launch_bounds__(256)
-cull_mask_kernel(const __grid_constant__ FwdBatch b, const VolGeom g, int isx, int isy, int tx, int ty,
-                 int tz, int nbx, int nby, long long nblocks, unsigned long long *__restrict__ masks,
-                 unsigned long long *__restrict__ work)
+block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__ CentreBatch cb, const VolGeom g,
+                     int isx, int isy, int tx, int ty, int tz, int nbx, int nby, long long nblocks,
+                     unsigned long long *__restrict__ masks, float4 *__restrict__ centres,
+                     unsigned long long *__restrict__ work)
 {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long done = 0;
     if (q < nblocks) {
         const int bx = (int)(q % nbx), by = (int)((q / nbx) % nby), bz = (int)(q / ((long long)nbx * nby));
         const int x0 = bx * tx, y0 = by * ty, z0 = bz * tz;
-        done = block_mask(b, g, isx, isy, x0, y0, z0, min(x0 + tx, g.L) - 1, min(y0 + ty, g.L) - 1,
-                          min(z0 + tz, g.L) - 1, &masks[q]);
+        const int x1 = min(x0 + tx, g.L) - 1, y1 = min(y0 + ty, g.L) - 1, z1 = min(z0 + tz, g.L) - 1;
+        unsigned long long m = 0;
+        for (int i = 0; i < b.n; ++i) {
+            if (masks && footprint_hits(b, i, g, isx, isy, x0, y0, z0, x1, y1, z1))
+                m |= 1ull << i;
+            if constexpr (CENTRES)
+                centres[(size_t)i * nblocks + q] = block_centre(cb, i, x0 + x1, y0 + y1, z0 + z1);
+        }
+        if (masks) {
+            masks[q] = m;
+            done = (unsigned long long)__popcll(m) * (x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1);
+        }
     }
     for (int o = 16; o > 0; o >>= 1)
         done += __shfl_down_sync(0xffffffffu, done, o);
-    if ((threadIdx.x & 31) == 0 && done)
+    if ((threadIdx.x & 31) == 0 && done && work)
         atomicAdd(work, done);
 }
 
-cudaError_t launch_cull_masks(const FwdBatch &b, const VolGeom &g, int isx, int isy, int lanes_x,
-                              unsigned long long *masks, unsigned long long *work, cudaStream_t s)
+cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const VolGeom &g, int isx, int isy,
+                                 int lanes_x, unsigned long long *masks, float4 *centres,
+                                 unsigned long long *work, cudaStream_t s)
 {
+    if (b.n <= 0 || (!masks && !centres))
+        return cudaSuccess;
     int tx, ty, tz;
     layout_tile(lanes_x, &tx, &ty, &tz);
     const int nbx = (g.L + tx - 1) / tx, nby = (g.L + ty - 1) / ty;
     const long long nblocks = fwd_blocks(g.L, lanes_x);
-    cull_mask_kernel<<<(unsigned)((nblocks + 255) / 256), 256, 0, s>>>(b, g, isx, isy, tx, ty, tz, nbx, nby,
-                                                                      nblocks, masks, work);
+    const unsigned grid = (unsigned)((nblocks + 255) / 256);
+    if (centres && cb) {
+        block_prepass_kernel<true><<<grid, 256, 0, s>>>(b, *cb, g, isx, isy, tx, ty, tz, nbx, nby, nblocks, masks,
+                                                        centres, work);
+    } else {
+        static const CentreBatch none = {};
+        block_prepass_kernel<false><<<grid, 256, 0, s>>>(b, none, g, isx, isy, tx, ty, tz, nbx, nby, nblocks, masks,
+                                                         nullptr, work);
+    }
     return cudaGetLastError();
+}
+
+// Host side of the centring records: rows holds, per projection, the
+// per-projection-centred rows u', v', w in float64 (n x 3 x 4).  Each row is
+// stored as its value at voxel (0,0,0), X = O, and its change per half voxel
+// along x, y and z.
+void centre_batch(CentreBatch *cb, const double *rows, int n, const double O[3], double R)
+{
+    auto split = [](double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < 3; ++r) {
+            const double *a = rows + 12 * i + 4 * r;
+            cb->c[i][r][0] = split(a[0] * O[0] + a[1] * O[1] + a[2] * O[2] + a[3]);
+            cb->c[i][r][1] = split(a[0] * 0.5 * R);
+            cb->c[i][r][2] = split(a[1] * 0.5 * R);
+            cb->c[i][r][3] = split(a[2] * 0.5 * R);
+        }
 }
 
 // Warp layouts (bp_set_option BP_OPT_LANES_X): 8, 16, 32 = lanes along x
@@ -250,31 +395,31 @@ cudaError_t launch_cull_masks(const FwdBatch &b, const VolGeom &g, int isx, int 
 // per lane (instead of 4).
 template <int KIND, bool IEEE>
 static cudaError_t launch_kind(const FwdBatch &b, float *vol, const VolGeom &g, bool acc, int layout,
-                               const unsigned long long *m, cudaStream_t s)
+                               const unsigned long long *m, const float4 *c, cudaStream_t s)
 {
     switch (layout) {
-    case 32: return launch_lx<KIND, IEEE, 32, 1>(b, vol, g, acc, m, s);
-    case 16: return launch_lx<KIND, IEEE, 16, 1>(b, vol, g, acc, m, s);
-    case 44: return launch_lx<KIND, IEEE, 4, 4>(b, vol, g, acc, m, s);
-    case 42: return launch_lx<KIND, IEEE, 4, 2>(b, vol, g, acc, m, s);
-    case 82: return launch_lx<KIND, IEEE, 8, 2>(b, vol, g, acc, m, s);
-    case 24: return launch_lx<KIND, IEEE, 2, 4>(b, vol, g, acc, m, s);
-    case 108: return launch_lx<KIND, IEEE, 8, 1, 8>(b, vol, g, acc, m, s);
-    default: return launch_lx<KIND, IEEE, 8, 1>(b, vol, g, acc, m, s);
+    case 32: return launch_lx<KIND, IEEE, 32, 1>(b, vol, g, acc, m, c, s);
+    case 16: return launch_lx<KIND, IEEE, 16, 1>(b, vol, g, acc, m, c, s);
+    case 44: return launch_lx<KIND, IEEE, 4, 4>(b, vol, g, acc, m, c, s);
+    case 42: return launch_lx<KIND, IEEE, 4, 2>(b, vol, g, acc, m, c, s);
+    case 82: return launch_lx<KIND, IEEE, 8, 2>(b, vol, g, acc, m, c, s);
+    case 24: return launch_lx<KIND, IEEE, 2, 4>(b, vol, g, acc, m, c, s);
+    case 108: return launch_lx<KIND, IEEE, 8, 1, 8>(b, vol, g, acc, m, c, s);
+    default: return launch_lx<KIND, IEEE, 8, 1>(b, vol, g, acc, m, c, s);
     }
 }
 
 cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int tex_kind,
                           bool accumulate, bool ieee_rcp, int lanes_x, const unsigned long long *masks,
-                          cudaStream_t s)
+                          const float4 *centres, cudaStream_t s)
 {
     if (b.n <= 0)
         return cudaSuccess;
     if (tex_kind == kTexFloat)
-        return ieee_rcp ? launch_kind<kTexFloat, true>(b, vol, g, accumulate, lanes_x, masks, s)
-                        : launch_kind<kTexFloat, false>(b, vol, g, accumulate, lanes_x, masks, s);
-    return ieee_rcp ? launch_kind<kTexBF16, true>(b, vol, g, accumulate, lanes_x, masks, s)
-                    : launch_kind<kTexBF16, false>(b, vol, g, accumulate, lanes_x, masks, s);
+        return ieee_rcp ? launch_kind<kTexFloat, true>(b, vol, g, accumulate, lanes_x, masks, centres, s)
+                        : launch_kind<kTexFloat, false>(b, vol, g, accumulate, lanes_x, masks, centres, s);
+    return ieee_rcp ? launch_kind<kTexBF16, true>(b, vol, g, accumulate, lanes_x, masks, nullptr, s)
+                    : launch_kind<kTexBF16, false>(b, vol, g, accumulate, lanes_x, masks, nullptr, s);
 }
 
 // ---------------------------------------------------------------------------

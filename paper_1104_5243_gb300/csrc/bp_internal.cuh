@@ -54,20 +54,51 @@ struct VolGeom {
 // unit widens FP16 exactly) or raw 16-bit words holding BF16.
 enum TexKind { kTexFloat = 0, kTexBF16 = 1 };
 
+// Per-block centring (float32 form).  Centring once per projection leaves
+// |u'| up to the half-width of the volume's footprint (hundreds of pixels on
+// a full detector), and the float32 rounding of u' there is what limits the
+// accuracy.  With per-block centring, every (thread block, projection) gets
+// its own integer offsets ku_b = ku + dku, kv_b = kv + dkv (the pixel the
+// block centre projects to).  It also gets the centred rows' values at the
+// block centre, uw_c = (row_u - (ku_b - 1) row_w) . (x_c, 1) and likewise
+// vw_c.  These are computed as float-float sums (about 44 significant bits)
+// and rounded to float32 once.  The kernel then works with offsets from the
+// block centre, where every float32 quantity stays small.
+//
+// CentreBatch: for each projection and row r = (u', v', w) of the
+// per-projection-centred matrix, the row's value at voxel (0,0,0) and its
+// change per half voxel along x, y, z, each a float64 value split into a
+// float32 (hi, lo) pair.  A block is centred on the centre of its voxel box
+// clipped to the volume, at half-integer voxel indices.  The pre-pass writes
+// one record per (block, projection), float4 (uw_c, vw_c, dku, dkv), at
+// index projection * blocks + block.
+struct CentreBatch {
+    float2 c[kMaxBatch][3][4];
+};
+
+// Fills cb from the float64 centred rows (n x 3 x 4: u', v', w).
+void centre_batch(CentreBatch *cb, const double *rows, int n, const double O[3], double R);
+
 // masks: one 64-bit word per thread block of the texture kernel, bit i set
 // when projection i of the batch can reach the block's voxels (NULL: no
-// culling).  Built by launch_cull_masks for the same layout.
+// culling).  centres: the per-block centring records (NULL: per-projection
+// centring; only the float-channel kind supports it).  Both are built by
+// launch_block_prepass for the same layout.
 cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int tex_kind,
                           bool accumulate, bool ieee_rcp, int lanes_x, const unsigned long long *masks,
-                          cudaStream_t s);
+                          const float4 *centres, cudaStream_t s);
 
-// Number of thread blocks of the texture kernel for a layout, and the mask
-// pre-pass: a block's bit for projection i is cleared when the projections
-// of its voxel box miss the detector by more than a pixel (every term of
-// those updates is exactly zero).
+// Number of thread blocks of the texture kernel for a layout, and the
+// per-block pre-pass (one thread per block):
+// - masks (if not NULL): a block's bit for projection i is cleared when the
+//   projections of its voxel box miss the detector by more than a pixel
+//   (every term of those updates is exactly zero);
+// - centres (if not NULL, with cb): the block centring records;
+// - work (if not NULL): the kept updates are added to *work.
 long long fwd_blocks(int L, int lanes_x);
-cudaError_t launch_cull_masks(const FwdBatch &b, const VolGeom &g, int isx, int isy, int lanes_x,
-                              unsigned long long *masks, unsigned long long *work, cudaStream_t s);
+cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const VolGeom &g, int isx, int isy,
+                                 int lanes_x, unsigned long long *masks, float4 *centres,
+                                 unsigned long long *work, cudaStream_t s);
 
 // smem: accumulate each block's footprint in shared memory (kAdjTile pixels
 // at most) and add it to the image with one atomic per touched pixel.

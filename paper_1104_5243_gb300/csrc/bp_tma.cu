@@ -134,6 +134,59 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// The 4 updates of one consumer lane for projection i, reading the corner
+// pairs from the staged tile (SMEM) or from the global pair image; the two
+// forms are separate loop bodies so neither carries the other's work.
+template <int KIND, bool IEEE, bool SMEM>
+__device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, int cu, int cv,
+                                            const typename Pairs<KIND>::T *tile, const float (&Xv)[2], float Y,
+                                            const float (&Zv)[2], float (&acc)[4])
+{
+    using P = Pairs<KIND>;
+    using T = typename P::T;
+    constexpr int BU = TmaBox<KIND>::BU, kBufElems = BU * TmaBox<KIND>::BV;
+    const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz) {
+        const float bu = fmaf(ru.y, Y, fmaf(ru.z, Zv[kz], ru.w));
+        const float bv = fmaf(rv.y, Y, fmaf(rv.z, Zv[kz], rv.w));
+        const float bw = fmaf(rw.y, Y, fmaf(rw.z, Zv[kz], rw.w));
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx) {
+            const float uw = fmaf(ru.x, Xv[kx], bu);
+            const float vw = fmaf(rv.x, Xv[kx], bv);
+            const float w = fmaf(rw.x, Xv[kx], bw);
+            const float r = recip_tma<IEEE>(w);
+            const float u = uw * r, v = vw * r;
+            const float fu0 = floorf(u), fv0 = floorf(v);
+            const int col = int_of_integral(fu0) + cu;
+            const int row = int_of_integral(fv0) + cv;
+            float2 top, bot;
+            if constexpr (SMEM) {
+                // the corner-based box covers every voxel of the volume with a
+                // pixel of margin; the clamp only guards the array for lanes
+                // beyond a ragged edge
+                const int idx = (int)min((unsigned)(row * BU + col), (unsigned)(kBufElems - BU - 1));
+                top = P::unpack(tile[idx]);
+                bot = P::unpack(tile[idx + BU]);
+            } else {
+                // rows outside the detector are zero
+                const T *img = reinterpret_cast<const T *>(b.img[i]);
+                const bool cok = col >= 0 && col <= b.isx;
+                const T *p = img + (long long)row * b.pitch + col;
+                const T zero{};
+                top = P::unpack(cok && row >= 0 && row < b.isy ? p[0] : zero);
+                bot = P::unpack(cok && row + 1 >= 0 && row + 1 < b.isy ? p[b.pitch] : zero);
+            }
+            const float fu = u - fu0, fv = v - fv0;
+            const float t = fmaf(fu, top.y - top.x, top.x);
+            const float bt = fmaf(fu, bot.y - bot.x, bot.x);
+            const float fx = fmaf(fv, bt - t, t);
+            acc[kz * 2 + kx] = fmaf(fx, r * r, acc[kz * 2 + kx]);
+        }
+    }
+}
+
 // Warp-specialised pipeline: warps 0..7 compute (256 consumer threads, 4
 // voxels each), warp 8 is the producer.  Stage s of the kTmaStages-deep ring
 // has a "full" barrier (the producer's arrival, plus the TMA bytes when a
@@ -274,51 +327,11 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
             break;
         }
         const int4 mt = meta[s];
-        const int mode = mt.x, cu = mt.y, cv = mt.z;
-        if (mode != 0) {
-            const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
-#pragma unroll
-            for (int kz = 0; kz < 2; ++kz) {
-                const float bu = fmaf(ru.y, Y, fmaf(ru.z, Zv[kz], ru.w));
-                const float bv = fmaf(rv.y, Y, fmaf(rv.z, Zv[kz], rv.w));
-                const float bw = fmaf(rw.y, Y, fmaf(rw.z, Zv[kz], rw.w));
-#pragma unroll
-                for (int kx = 0; kx < 2; ++kx) {
-                    const float uw = fmaf(ru.x, Xv[kx], bu);
-                    const float vw = fmaf(rv.x, Xv[kx], bv);
-                    const float w = fmaf(rw.x, Xv[kx], bw);
-                    const float r = recip_tma<IEEE>(w);
-                    const float u = uw * r, v = vw * r;
-                    const float fu0 = floorf(u), fv0 = floorf(v);
-                    const int col = int_of_integral(fu0) + cu;
-                    const int row = int_of_integral(fv0) + cv;
-                    float2 top, bot;
-                    if (mode == 1) {
-                        // the corner-based box covers every voxel of the
-                        // volume with a pixel of margin; the clamp only
-                        // guards the array for lanes beyond a ragged edge
-                        const int idx = (int)min((unsigned)(row * BU + col), (unsigned)(kBufElems - BU - 1));
-                        const T *p = buf[s] + idx;
-                        top = P::unpack(p[0]);
-                        bot = P::unpack(p[BU]);
-                    } else {
-                        // footprint larger than the box: read the pair image
-                        // directly, rows outside the detector are zero
-                        const T *img = reinterpret_cast<const T *>(b.img[i]);
-                        const bool cok = col >= 0 && col <= b.isx;
-                        const T *p = img + (long long)row * b.pitch + col;
-                        const T zero{};
-                        top = P::unpack(cok && row >= 0 && row < b.isy ? p[0] : zero);
-                        bot = P::unpack(cok && row + 1 >= 0 && row + 1 < b.isy ? p[b.pitch] : zero);
-                    }
-                    const float fu = u - fu0, fv = v - fv0;
-                    const float t = fmaf(fu, top.y - top.x, top.x);
-                    const float bt = fmaf(fu, bot.y - bot.x, bot.x);
-                    const float fx = fmaf(fv, bt - t, t);
-                    acc[kz * 2 + kx] = fmaf(fx, r * r, acc[kz * 2 + kx]);
-                }
-            }
-        }
+        const int mode = mt.x;
+        if (mode == 1)        // tile in shared memory (the common case)
+            tma_updates<KIND, IEEE, true>(b, i, mt.y, mt.z, buf[s], Xv, Y, Zv, acc);
+        else if (mode == 2)   // footprint larger than the tile
+            tma_updates<KIND, IEEE, false>(b, i, mt.y, mt.z, buf[s], Xv, Y, Zv, acc);
         __syncwarp();
         if (lane == 0)
             mbar_arrive(&empty[s]);   // this warp is done with stage s

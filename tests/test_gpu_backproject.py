@@ -160,11 +160,13 @@ def test_gpu_matrices_match_oracle():
         np.testing.assert_allclose(api.carm_matrices(scan), oracle.carm_matrices(scan), rtol=1e-14, atol=1e-14)
 
 
-@pytest.mark.parametrize("L,dtype,tol", [(512, "f32", FP32_TOL), (512, "f16", FP16_TOL)])
+@pytest.mark.parametrize("L,dtype,tol", [(512, "f32", FP32_TOL), (512, "f16", FP16_TOL), (512, "bf16", BF16_TOL),
+                                         (1024, "f16", FP16_TOL), (1024, "bf16", BF16_TOL)])
 def test_full_size_sampled_voxels(L, dtype, tol):
-    """512^3 x 496 x 1248x960, uniform timing stack, in the launch
-    configuration the benchmark times (batches of 64, device input); the
-    oracle evaluates 4096 sampled voxels one by one."""
+    """512^3 (and the 1024^3 precision form) x 496 x 1248x960, uniform timing
+    stack, in the launch configuration the benchmark times (batches of 64,
+    device input, default path); the oracle evaluates 4096 sampled voxels one
+    by one."""
     api = native()
     scan, vol = synth.SCANS["full"], synth.Volume(L)
     A = oracle.carm_matrices(scan)
@@ -177,19 +179,66 @@ def test_full_size_sampled_voxels(L, dtype, tol):
     ref = oracle.backproject_voxels(vol.L, vol.R, vol.O, stack, A, idx)
     g = got[torch.from_numpy(idx).cuda()].cpu().numpy()
     err = rel_l2(g, ref)
-    print(f"{L}^3 {dtype} sampled rel-L2 {err:.3e} max-rel {np.max(np.abs(g - ref) / np.maximum(np.abs(ref), 1e-30)):.3e}")
+    print(f"{L}^3 {dtype} sampled rel-L2 {err:.3e} max-abs {np.abs(g - ref).max():.3e} "
+          f"(max |ref| {np.abs(ref).max():.3e})")
     assert err <= tol
     bp.close()
 
 
+@pytest.mark.parametrize("dtype,tol", [("f32", FP32_TOL), ("f16", FP16_TOL)])
+def test_full_detector_ramp_filtered_phantom(dtype, tol):
+    """512^3 with the full 1248x960 detector and a ramp-filtered 50-ellipsoid
+    phantom (seed 2), every 16th of the 496 projections (the oracle computes
+    the line integrals, the FDK filtering and 4096 sampled voxels)."""
+    api = native()
+    full = synth.SCANS["full"]
+    A = oracle.carm_matrices(full)[::16]
+    betas = full.betas[::16]
+    sub = synth.Scan(n=len(betas), isx=full.isx, isy=full.isy, pitch=full.pitch,
+                     scan_deg=float(np.degrees(betas[-1] - betas[0])))
+    vol = synth.Volume(512)
+    ell = synth.ellipsoids(50, seed=2, scan=full)
+    lines = oracle.ellipsoid_project(A, full.isx, full.isy, ell)
+    # cosine weights only: the subsampled arc is shorter than 180 degrees plus
+    # the fan, so Parker weights do not apply (FDK quality is not at stake)
+    q = oracle.ramp_filter(oracle.fdk_preweight(sub, lines, parker=False,
+                                                scale=np.radians(200.0) / 495 * 16),
+                           oracle.iso_pitch(full)).astype(np.float32)
+    idx = np.random.default_rng(8).integers(0, 512 ** 3, size=4096)
+    ref = oracle.backproject_voxels(vol.L, vol.R, vol.O, q, A, idx)
+    from paper_1104_5243_gb300 import _native as N
+    errs = {}
+    for centre in ((1, 0) if dtype == "f32" else (1,)):
+        bp = api.Backprojector(vol.L, vol.R, vol.O, full.isx, full.isy, dtype=dtype)
+        bp.set_option(N.BP_OPT_BLOCK_CENTRE, centre)
+        bp.add_projections(torch.from_numpy(q).cuda(), A)
+        got = bp.finalize().view(-1)
+        bp.close()
+        g = got[torch.from_numpy(idx).cuda()].cpu().numpy()
+        errs[centre] = rel_l2(g, ref)
+        print(f"512^3 phantom {dtype} block_centre={centre} sampled rel-L2 {errs[centre]:.3e} "
+              f"max-abs {np.abs(g - ref).max():.3e}")
+    assert errs[1] <= tol
+    if dtype == "f32":
+        # centring per block instead of per projection: u', v' stay within a
+        # block's footprint, so their float32 rounding is several times smaller
+        assert errs[1] * 4 <= errs[0]
+
+
 # ---------------------------------------------------------------------------
-# TMA / shared-memory data path: same arithmetic as the texture path, so the
-# volumes must agree bit for bit (culled bricks only skip exact zeros).
-def run_path(vol, scan, A, q, path, dtype="f32"):
+# TMA / shared-memory data path: same arithmetic as the texture path with
+# per-projection centring, so the volumes agree bit for bit (culled bricks
+# only skip exact zeros).
+def run_path(vol, scan, A, q, path, dtype="f32", block_centre=None):
+    """block_centre=None keeps the default; the TMA path always centres per
+    projection, so bit-identity with it needs block_centre=0 on the texture
+    path for float32 projections."""
     api = native()
     from paper_1104_5243_gb300 import _native as N
     bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype)
     bp.set_option(N.BP_OPT_PATH, path)
+    if block_centre is not None:
+        bp.set_option(N.BP_OPT_BLOCK_CENTRE, block_centre)
     bp.add_projections(torch.from_numpy(np.ascontiguousarray(q)).cuda(), A)
     out = bp.finalize().cpu()
     taken = bp.last_path
@@ -200,12 +249,17 @@ def run_path(vol, scan, A, q, path, dtype="f32"):
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_tma_path_is_bit_identical_to_texture_path(dtype):
     scan, vol, A, ell, q, ref = tiny_phantom_case()
-    tex, p1 = run_path(vol, scan, A, q, 1, dtype)
+    tex, p1 = run_path(vol, scan, A, q, 1, dtype, block_centre=0)
     tma, p2 = run_path(vol, scan, A, q, 2, dtype)
     assert (p1, p2) == ("texture", "tma")
     assert torch.equal(tex, tma)
     tol = {"f32": FP32_TOL, "f16": FP16_TOL, "bf16": BF16_TOL}[dtype]
     assert rel_l2(tma.numpy(), ref) <= tol
+    # the default texture path (per-block centring for float32) matches too
+    blk, _ = run_path(vol, scan, A, q, 1, dtype)
+    assert rel_l2(blk.numpy(), ref) <= tol
+    if dtype != "f32":
+        assert torch.equal(blk, tex)
 
 
 @pytest.mark.parametrize("L,isx,isy,n", [(37, 53, 41, 70), (1, 7, 5, 3), (40, 24, 10, 20)])
@@ -215,10 +269,12 @@ def test_tma_path_ragged_and_partial_detector(L, isx, isy, n):
     A = oracle.carm_matrices(scan)
     q = np.random.default_rng(L + n).standard_normal((n, isy, isx)).astype(np.float32)
     ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
-    tex, _ = run_path(vol, scan, A, q, 1)
+    tex, _ = run_path(vol, scan, A, q, 1, block_centre=0)
     tma, _ = run_path(vol, scan, A, q, 2)
     assert torch.equal(tex, tma)
     assert rel_l2(tma.numpy(), ref) <= FP32_TOL
+    blk, _ = run_path(vol, scan, A, q, 1)
+    assert rel_l2(blk.numpy(), ref) <= FP32_TOL
 
 
 def test_tma_global_fallback_when_footprints_exceed_the_tile():
@@ -229,7 +285,7 @@ def test_tma_global_fallback_when_footprints_exceed_the_tile():
     vol = synth.Volume(256)
     A = oracle.carm_matrices(scan)
     q = synth.uniform_stack(scan.n, scan.isy, scan.isx, seed=11)
-    tex, _ = run_path(vol, scan, A, q, 1)
+    tex, _ = run_path(vol, scan, A, q, 1, block_centre=0)
     tma, _ = run_path(vol, scan, A, q, 2)
     assert torch.equal(tex, tma)
     idx = np.random.default_rng(1).integers(0, 256 ** 3, size=512)
@@ -242,9 +298,11 @@ def test_automatic_path_choice():
     A = oracle.carm_matrices(scan)[:8]
     q = synth.uniform_stack(8, scan.isy, scan.isx, seed=3)
     auto, p_auto = run_path(synth.Volume(128), scan, A, q, 0)
+    tex, p_tex = run_path(synth.Volume(128), scan, A, q, 1)
     tma, p_tma = run_path(synth.Volume(128), scan, A, q, 2)
-    assert (p_auto, p_tma) == ("texture", "tma")
-    assert torch.equal(auto, tma)
+    assert (p_auto, p_tex, p_tma) == ("texture", "texture", "tma")
+    assert torch.equal(auto, tex)
+    assert rel_l2(auto.numpy(), tma.numpy()) <= FP32_TOL
 
 
 def test_reciprocal_modes_accuracy_table():
@@ -261,8 +319,9 @@ def test_reciprocal_modes_accuracy_table():
     assert abs(p_a - p_i) < 3.0
 
 
+@pytest.mark.parametrize("block_centre", [1, 0])
 @pytest.mark.parametrize("L,name", [(64, "tiny"), (37, None), (96, "half")])
-def test_culling_is_bit_exact(L, name):
+def test_culling_is_bit_exact(L, name, block_centre):
     """Skipping (block, projection) pairs whose footprint misses the detector
     must not change a single bit (those terms are exactly zero)."""
     api = native()
@@ -278,6 +337,7 @@ def test_culling_is_bit_exact(L, name):
         bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
         bp.set_option(N.BP_OPT_PATH, 1)
         bp.set_option(N.BP_OPT_CULL, cull)
+        bp.set_option(N.BP_OPT_BLOCK_CENTRE, block_centre)
         bp.add_projections(q, A)
         outs.append(bp.finalize().cpu())
         bp.close()
