@@ -65,6 +65,19 @@ def roofline_peak_gups(sm_mhz: float, sms: int, gather_per_sm_clk: float) -> dic
     return bounds
 
 
+def algorithmic_bytes(L: int, n: int, isx: int, isy: int, form: str, computed_fraction: float) -> int:
+    """Bytes one mid-step launch of the backprojection kernel must move: the
+    volume read and written once, each of the n projections read once, and
+    for the FP32 form the per-block centring records (3 x 16 B) of the
+    (block, projection) pairs it computes (default layout: 32 x 8 x 4-voxel
+    blocks)."""
+    total = 8 * L ** 3 + n * isx * isy * (4 if form == "f32" else 2)
+    if form == "f32":
+        blocks = -(-L // 32) * -(-L // 8) * -(-L // 4)
+        total += int(48 * n * blocks * computed_fraction)
+    return int(total)
+
+
 def ncu_traffic(kernel_file: str, profile: str):
     """DRAM bytes per launch from a committed ncu summary, or None when the
     summary is missing or the kernel source changed since it was captured."""
@@ -418,7 +431,8 @@ def main():
         "avg_launch_ms": round(k["kernel_ms"] / max(k["launches"], 1), 4),
         "launches": k["launches"],
         "traffic": traffic,
-        "algorithmic_bytes_per_launch": int(vol.L ** 3 * 8 + min(scan.n, 64) * scan.isx * scan.isy * 4),
+        "algorithmic_bytes_per_launch": algorithmic_bytes(vol.L, min(scan.n, 64), scan.isx, scan.isy, head,
+                                                          k["computed_fraction"]),
     }
     cpu = None
     if not args.no_cpu_baseline:

@@ -98,8 +98,9 @@ typedef enum {
     BP_OPT_HOST_DIRECT = 7,
     /* BP_F32 projections on the texture path: 1 (default) centre the detector
      * coordinates per block of voxels and projection, 0 once per projection.
-     * Per-block centring costs a per-block pre-pass and 16 bytes of device
-     * memory per (block, projection of a batch) (128 MiB for a 512^3 volume),
+     * Per-block centring costs a per-block pre-pass and 2 x 48 bytes of
+     * device memory per (block, projection of a batch) (768 MiB for a 512^3
+     * volume),
      * and cuts the float32 rounding of u and v by the ratio of block to volume
      * footprint (rel-L2 5e-7 instead of 1e-5 on a full 1248x960 detector).
      * 16-bit storage and the TMA path always centre per projection. */

@@ -558,7 +558,7 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                         CTX_CK(c, cudaFree(c->centres[s]));
                     c->centres[s] = nullptr;
                     c->centre_blocks[s] = 0;
-                    CTX_CK(c, cudaMalloc((void **)&c->centres[s], sizeof(float4) * kMaxBatch * nb));
+                    CTX_CK(c, cudaMalloc((void **)&c->centres[s], sizeof(float4) * 3 * kMaxBatch * nb));
                     c->centre_blocks[s] = nb;
                 }
                 centres = c->centres[s];

@@ -89,65 +89,70 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
     const int y = blockIdx.y * TY + (threadIdx.x >> 5) * LY + ty;
     const int z = blockIdx.z * LZ + tz;
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    // BLK: the block's centring records, one per projection, staged once
-    __shared__ float4 cen[BLK ? kMaxBatch : 1];
+    // projections that can reach this block (all of them without culling)
+    const unsigned long long visible = masks ? masks[blk] : ~0ull;
+    // BLK: the block's centring records of those projections (three float4
+    // planes: u row, v row, (w_c, gather offsets)), staged once
+    __shared__ float4 cen[BLK ? 3 * kMaxBatch : 1];
     if constexpr (BLK) {
-        if (threadIdx.x < b.n)
-            cen[threadIdx.x] = centres[(size_t)threadIdx.x * gridDim.x * gridDim.y * gridDim.z + blk];
+        const size_t nblk = (size_t)gridDim.x * gridDim.y * gridDim.z;
+        if (threadIdx.x < 3 * kMaxBatch) {
+            const int j = threadIdx.x / kMaxBatch, i = threadIdx.x % kMaxBatch;
+            if (i < b.n && ((visible >> i) & 1ull))
+                cen[threadIdx.x] = centres[((size_t)j * kMaxBatch + i) * nblk + blk];
+        }
         __syncthreads();
     }
     if (y >= L || z >= L)
         return;
 
-    // absolute voxel coordinates (the w row), and with BLK the offsets from
-    // the centre of the block's voxel box clipped to the volume (the u and v
-    // rows); the centre index (x0 + x1) / 2 is a multiple of 1/2, so the
-    // offsets are exact before the product with R
+    // Voxel coordinates: absolute, or with BLK offsets from the centre of the
+    // block's voxel box clipped to the volume, (x0 + x1) / 2 etc.  The centre
+    // index is a multiple of 1/2, so the offsets are exact before the product
+    // with R.
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * LZ;
     const float hx = 0.5f * (float)(x0 + min(x0 + TX, L) - 1);
     const float hy = 0.5f * (float)(y0 + min(y0 + TY, L) - 1);
     const float hz = 0.5f * (float)(z0 + min(z0 + LZ, L) - 1);
-    float X[VPL], dX[VPL];
+    float X[VPL];
 #pragma unroll
-    for (int k = 0; k < VPL; ++k) {
-        X[k] = fmaf(g.R, (float)(xb + LX * k), g.Ox);
-        dX[k] = BLK ? g.R * ((float)(xb + LX * k) - hx) : X[k];
-    }
-    const float Y = fmaf(g.R, (float)y, g.Oy);
-    const float Z = fmaf(g.R, (float)z, g.Oz);
-    const float dY = BLK ? g.R * ((float)y - hy) : Y;
-    const float dZ = BLK ? g.R * ((float)z - hz) : Z;
+    for (int k = 0; k < VPL; ++k)
+        X[k] = BLK ? g.R * ((float)(xb + LX * k) - hx) : fmaf(g.R, (float)(xb + LX * k), g.Ox);
+    const float Y = BLK ? g.R * ((float)y - hy) : fmaf(g.R, (float)y, g.Oy);
+    const float Z = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)z, g.Oz);
 
     float acc[VPL];
 #pragma unroll
     for (int k = 0; k < VPL; ++k)
         acc[k] = 0.f;
-    // projections that can reach this block (all of them without culling)
-    const unsigned long long visible = masks ? masks[blk] : ~0ull;
 #pragma unroll 1
     for (int i = 0; i < b.n; ++i) {
         if (!((visible >> i) & 1ull))
             continue;   // every term of this projection is exactly zero here
-        float4 ru = b.m[i][0], rv = b.m[i][1];
-        const float4 rw = b.m[i][2];
-        float2 kc = b.k[i];
-        const cudaTextureObject_t t = b.tex[i];
+        float4 ru, rv, rw = b.m[i][2];
+        float2 kc;
         if constexpr (BLK) {
-            // recentre on (ku + dku, kv + dkv): row_u'' = row_u' - dku row_w,
-            // whose value at the block centre is c.x
-            const float4 c = cen[i];
-            ru = make_float4(fmaf(-c.z, rw.x, ru.x), fmaf(-c.z, rw.y, ru.y), fmaf(-c.z, rw.z, ru.z), c.x);
-            rv = make_float4(fmaf(-c.w, rw.x, rv.x), fmaf(-c.w, rw.y, rv.y), fmaf(-c.w, rw.z, rv.z), c.y);
-            kc = make_float2(kc.x + c.z, kc.y + c.w);
+            // rows recentred on the block: (row_u'' x, y, z, value at the
+            // block centre), likewise v, and (w_c, gather offsets)
+            ru = cen[i];
+            rv = cen[kMaxBatch + i];
+            const float4 c = cen[2 * kMaxBatch + i];
+            rw.w = c.x;
+            kc = make_float2(c.y, c.z);
+        } else {
+            ru = b.m[i][0];
+            rv = b.m[i][1];
+            kc = b.k[i];
         }
+        const cudaTextureObject_t t = b.tex[i];
         // Part 1: geometry; the y, z terms are shared by the lane's voxels.
-        const float bu = fmaf(ru.y, dY, fmaf(ru.z, dZ, ru.w));
-        const float bv = fmaf(rv.y, dY, fmaf(rv.z, dZ, rv.w));
+        const float bu = fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w));
+        const float bv = fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w));
         const float bw = fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w));
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
-            const float uw = fmaf(ru.x, dX[k], bu);
-            const float vw = fmaf(rv.x, dX[k], bv);
+            const float uw = fmaf(ru.x, X[k], bu);
+            const float vw = fmaf(rv.x, X[k], bv);
             const float w = fmaf(rw.x, X[k], bw);
             const float r = recip<IEEE>(w);
             const float u = uw * r, v = vw * r;       // centred: u - ku + 1
@@ -284,12 +289,20 @@ __device__ bool footprint_hits(const FwdBatch &b, int i, const VolGeom &g, int i
 }
 
 // Centring record of the block whose clipped voxel box has its centre at
-// voxel index (cx2, cy2, cz2) / 2, for projection i: the rows' values there
-// as float-float sums C + cx2 Hx + cy2 Hy + cz2 Hz, the offsets
-// dku = round(u'_c), dkv = round(v'_c), and the recentred values
-// uw_c - dku w_c, vw_c - dkv w_c rounded to float32 once.  The centre lies
-// in the volume, where the host has checked w > 0.
-__device__ float4 block_centre(const CentreBatch &cb, int i, int cx2, int cy2, int cz2)
+// voxel index (cx2, cy2, cz2) / 2, for projection i.  The rows' values there
+// are float-float sums C + cx2 Hx + cy2 Hy + cz2 Hz; with the offsets
+// dku = round(u'_c), dkv = round(v'_c) (any integer is valid; these make
+// u'' and v'' smallest near the centre) the record holds
+//   u: (row_u'' x, y, z, uw_c - dku w_c),  row_u'' = row_u' - dku row_w,
+//   v: the same for v,
+//   w: (w_c, ku + dku, kv + dkv, 0),
+// the centre values rounded to float32 once.  The centre lies in the volume,
+// where the host has checked w > 0.
+struct BlockRec {
+    float4 u, v, w;
+};
+
+__device__ BlockRec block_centre(const FwdBatch &b, const CentreBatch &cb, int i, int cx2, int cy2, int cz2)
 {
     Ff val[3];
 #pragma unroll
@@ -301,19 +314,25 @@ __device__ float4 block_centre(const CentreBatch &cb, int i, int cx2, int cy2, i
         val[r] = ff_add(ff_add({c[0].x, c[0].y}, sx), ff_add(sy, sz));
     }
     float dku = rintf(val[0].hi / val[2].hi), dkv = rintf(val[1].hi / val[2].hi);
-    // any integer is a valid offset; keep them exact and finite
     if (!(fabsf(dku) <= 1048576.f))
         dku = 0.f;
     if (!(fabsf(dkv) <= 1048576.f))
         dkv = 0.f;
     const Ff du = ff_mul_int(val[2], -dku), dv = ff_mul_int(val[2], -dkv);
-    return make_float4(ff_add(val[0], du).hi, ff_add(val[1], dv).hi, dku, dkv);
+    const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+    const float2 kc = b.k[i];
+    BlockRec rec;
+    rec.u = make_float4(fmaf(-dku, rw.x, ru.x), fmaf(-dku, rw.y, ru.y), fmaf(-dku, rw.z, ru.z), ff_add(val[0], du).hi);
+    rec.v = make_float4(fmaf(-dkv, rw.x, rv.x), fmaf(-dkv, rw.y, rv.y), fmaf(-dkv, rw.z, rv.z), ff_add(val[1], dv).hi);
+    rec.w = make_float4(val[2].hi, kc.x + dku, kc.y + dkv, 0.f);
+    return rec;
 }
 
 // One thread per block of the texture kernel, looping over the projections
 // of the batch (a warp-uniform index: the matrices are read from kernel
-// parameter space by broadcast).  Records are stored projection-major,
-// centres[i * nblocks + block], so a warp's stores are contiguous.  The kept
+// parameter space by broadcast).  Records are stored as three planes
+// (u, v, w parts), projection-major within each, centres[(part * 64 + i) *
+// nblocks + block], so a warp's stores are contiguous.  The kept
 // updates are summed per warp into the context's work counter (for the
 // roofline).
 template <bool CENTRES>
@@ -333,8 +352,12 @@ block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__
         for (int i = 0; i < b.n; ++i) {
             if (masks && footprint_hits(b, i, g, isx, isy, x0, y0, z0, x1, y1, z1))
                 m |= 1ull << i;
-            if constexpr (CENTRES)
-                centres[(size_t)i * nblocks + q] = block_centre(cb, i, x0 + x1, y0 + y1, z0 + z1);
+            if constexpr (CENTRES) {
+                const BlockRec rec = block_centre(b, cb, i, x0 + x1, y0 + y1, z0 + z1);
+                centres[((size_t)0 * kMaxBatch + i) * nblocks + q] = rec.u;
+                centres[((size_t)1 * kMaxBatch + i) * nblocks + q] = rec.v;
+                centres[((size_t)2 * kMaxBatch + i) * nblocks + q] = rec.w;
+            }
         }
         if (masks) {
             masks[q] = m;

@@ -60,8 +60,8 @@ enum TexKind { kTexFloat = 0, kTexBF16 = 1 };
 // accuracy.  With per-block centring, every (thread block, projection) gets
 // its own integer offsets ku_b = ku + dku, kv_b = kv + dkv (the pixel the
 // block centre projects to).  It also gets the centred rows' values at the
-// block centre, uw_c = (row_u - (ku_b - 1) row_w) . (x_c, 1) and likewise
-// vw_c.  These are computed as float-float sums (about 44 significant bits)
+// block centre, uw_c = (row_u - (ku_b - 1) row_w) . (x_c, 1), likewise vw_c,
+// and w_c.  These are computed as float-float sums (about 44 significant bits)
 // and rounded to float32 once.  The kernel then works with offsets from the
 // block centre, where every float32 quantity stays small.
 //
@@ -70,8 +70,9 @@ enum TexKind { kTexFloat = 0, kTexBF16 = 1 };
 // change per half voxel along x, y, z, each a float64 value split into a
 // float32 (hi, lo) pair.  A block is centred on the centre of its voxel box
 // clipped to the volume, at half-integer voxel indices.  The pre-pass writes
-// one record per (block, projection), float4 (uw_c, vw_c, dku, dkv), at
-// index projection * blocks + block.
+// three float4 per (block, projection): the u row recentred on the block,
+// (row_u'' x, y, z, uw_c), the same for v, and (w_c, ku_b, kv_b, 0), in three
+// planes at index (part * 64 + projection) * blocks + block.
 struct CentreBatch {
     float2 c[kMaxBatch][3][4];
 };
