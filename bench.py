@@ -33,47 +33,69 @@ sys.path.insert(0, ROOT)
 METRIC = "GUP/s at 512³×496 proj: FP32 vs FP16-projection form, % of roofline"
 UNIT = "GUP/s"
 
-# Roofline of the backprojection kernel (one update = one voxel x one
-# projection), per SM per clock, times SMs and the SM clock sampled under load:
-#   gather: the texture unit's 2x2-gather rate for the storage type, MEASURED
-#     on this GPU by bp_probe_gather (one gather per update);
-#   fp32_issue: 128 FP32 lanes per SM per clock over the kernel's 20.5 FP32-pipe
-#     instructions per update (from its source: 3 FFMA geometry + 1.5 FFMA of
-#     y/z terms per 4 voxels, 2 FMUL u/v, 2 floor, 2 FADD gather coordinate,
+# Roofline of the backprojection kernels (one update = one voxel x one
+# projection), per SM per clock, times SMs and the SM clock sampled under load.
+# Both kernels:
+#   fp32_pipe: 128 FP32 lanes over 20.5 FP32-pipe instructions per update
+#     (from the source: 3 FFMA geometry + 1.5 FFMA of y/z terms per 4 voxels,
+#     2 FMUL u/v, 2 floor, 2 FADD/FFMA gather coordinate or tile index,
 #     2 FADD fractions, 3 FADD + 3 FFMA interpolation, 1 FMUL + 1 FFMA weight
 #     and accumulate);
-#   mufu: 16 reciprocals per SM per clock, one per update.
-#   issue: 4 warp instructions per SM per clock (128 thread instructions)
-#     over the 27.6 instructions per update ncu counts for the kernel
-#     (smsp__inst_executed x 32 / updates, profiles/bp_fwd_kernel_*).
+#   mufu: 16 reciprocals per SM per clock, one per update;
+#   issue: 128 thread instructions per SM per clock over the instructions per
+#     computed update ncu counts for the kernel (smsp__inst_executed x 32 /
+#     computed updates; profiles/<kernel>_<form>_512x64.md).
+# Texture kernel (bp_fwd_kernel):
+#   gather: the texture unit's 2x2-gather rate for the storage type, MEASURED
+#     on this GPU by bp_probe_gather (one gather per update).
+# TMA kernel (bp_tma_kernel):
+#   smem: 128 B per SM per clock of shared-memory bandwidth over 23.1 B per
+#     update: two 8-byte pair loads, plus the TMA fill of the 114 x 32-pair box
+#     (29184 B) per 32 x 16 x 8-voxel brick and projection.
 FP32_PER_SM_CLK = 128.0
 FP32_INSTR_PER_UPDATE = 20.5
 ISSUE_PER_SM_CLK = 128.0
-INSTR_PER_UPDATE = 27.6
+INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 34.1}
 MUFU_PER_SM_CLK = 16.0
+SMEM_BYTES_PER_SM_CLK = 128.0
+TMA_SMEM_BYTES_PER_UPDATE = 16.0 + 114 * 32 * 8 / (32 * 16 * 8)
 
 
-def roofline_peak_gups(sm_mhz: float, sms: int, gather_per_sm_clk: float) -> dict:
+def roofline_peak_gups(path: str, form: str, sm_mhz: float, sms: int, gather_per_sm_clk: float) -> dict:
     f = sm_mhz * 1e6
     bounds = {
-        "gather": sms * gather_per_sm_clk * f / 1e9,
         "fp32_pipe": sms * FP32_PER_SM_CLK / FP32_INSTR_PER_UPDATE * f / 1e9,
-        "issue": sms * ISSUE_PER_SM_CLK / INSTR_PER_UPDATE * f / 1e9,
         "mufu": sms * MUFU_PER_SM_CLK * f / 1e9,
     }
+    if path == "tma":
+        bounds["smem"] = sms * SMEM_BYTES_PER_SM_CLK / TMA_SMEM_BYTES_PER_UPDATE * f / 1e9
+    else:
+        bounds["gather"] = sms * gather_per_sm_clk * f / 1e9
+    instr = INSTR_PER_UPDATE.get((path, form))
+    if instr is not None:
+        bounds["issue"] = sms * ISSUE_PER_SM_CLK / instr * f / 1e9
     bounds["min"] = min(bounds.values())
     return bounds
 
 
-def algorithmic_bytes(L: int, n: int, isx: int, isy: int, form: str, computed_fraction: float) -> int:
+def algorithmic_bytes(L: int, n: int, isx: int, isy: int, form: str, path: str, computed_fraction: float) -> int:
     """Bytes one mid-step launch of the backprojection kernel must move: the
-    volume read and written once, each of the n projections read once, and
-    for the FP32 form the per-block centring records (3 x 16 B) of the
-    (block, projection) pairs it computes (default layout: 32 x 8 x 4-voxel
-    blocks)."""
-    total = 8 * L ** 3 + n * isx * isy * (4 if form == "f32" else 2)
+    volume read and written once, each of the n projections read once (the
+    TMA path reads pair images: two pixels per element, row pitch padded to
+    16 B), and for the FP32 form the per-block centring records (3 x 16 B)
+    of the (block, projection) pairs it computes (texture blocks of
+    32 x 8 x 4 voxels, TMA bricks of 32 x 16 x 8)."""
+    px = 4 if form == "f32" else 2
+    if path == "tma":
+        align = 2 if form == "f32" else 4
+        pitch = -(-(isx + 1) // align) * align
+        total = 8 * L ** 3 + n * pitch * isy * 2 * px
+        tile = (32, 16, 8)
+    else:
+        total = 8 * L ** 3 + n * isx * isy * px
+        tile = (32, 8, 4)
     if form == "f32":
-        blocks = -(-L // 32) * -(-L // 8) * -(-L // 4)
+        blocks = -(-L // tile[0]) * -(-L // tile[1]) * -(-L // tile[2])
         total += int(48 * n * blocks * computed_fraction)
     return int(total)
 
@@ -411,17 +433,20 @@ def main():
     head = "f32" if "f32" in forms else next(iter(forms))
     f32 = forms[head]
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    peaks = {f: roofline_peak_gups(sm_mhz, sms, gather_rate[f]) for f in forms}
+    peaks = {f: roofline_peak_gups(path_taken.get(f, "texture"), f, sm_mhz, sms, gather_rate[f]) for f in forms}
     peak = peaks[head]
     k = kernel[head]
     achieved = k["kernel_gups_computed"]
-    traffic = ncu_traffic("bp_fwd.cu", f"bp_fwd_kernel_{head}_{args.L}.md") if args.n_proj == 496 else None
+    head_path = path_taken.get(head, "texture")
+    kname, ksrc = ("bp_tma_kernel", "bp_tma.cu") if head_path == "tma" else ("bp_fwd_kernel", "bp_fwd.cu")
+    traffic = ncu_traffic(ksrc, f"{kname}_{head}_{args.L}.md") if args.n_proj == 496 else None
+    basis = ("shared-memory bandwidth" if head_path == "tma" else "measured texture gather rate")
     roofline = {
-        "bound": "alu", "unit": UNIT, "kernel": f"bp_fwd_kernel ({head} projections)",
+        "bound": "alu", "unit": UNIT, "kernel": f"{kname} ({head} projections, {head_path} path)",
         "achieved": round(achieved, 2) if achieved else None,
         "peak": round(peak["min"], 1),
         "frac": round(achieved / peak["min"], 4) if achieved else None,
-        "peak_basis": "min(measured texture gather rate, instruction issue, FP32 pipe, MUFU) x SMs x sampled "
+        "peak_basis": f"min({basis}, instruction issue, FP32 pipe, MUFU) x SMs x sampled "
                       "SM clock; achieved counts the updates computed (culled blocks excluded)",
         "achieved_nominal": round(k["kernel_gups"], 2),
         "computed_fraction": round(k["computed_fraction"], 4),
@@ -432,7 +457,7 @@ def main():
         "launches": k["launches"],
         "traffic": traffic,
         "algorithmic_bytes_per_launch": algorithmic_bytes(vol.L, min(scan.n, 64), scan.isx, scan.isy, head,
-                                                          k["computed_fraction"]),
+                                                          head_path, k["computed_fraction"]),
     }
     cpu = None
     if not args.no_cpu_baseline:

@@ -80,8 +80,10 @@ typedef enum {
     /* Data path of the backprojection: 0 (default) automatic, 1 texture
      * gathers, 2 TMA-staged shared-memory tiles.  With the same centring
      * (BP_F16 / BP_BF16, or BP_OPT_BLOCK_CENTRE 0) the two give
-     * bit-identical volumes; the automatic choice is the texture path (with
-     * BP_OPT_CULL), the faster of the two on GB300 for every storage type.
+     * bit-identical volumes.  The automatic choice is the faster on GB300:
+     * the TMA path for BP_F32 projections, the texture path (with
+     * BP_OPT_CULL) for BP_F16 / BP_BF16.  The TMA path allocates two sets of
+     * 64 pair images on first use (1.2 GB for 1248x960 BP_F32).
      * bp_query(BP_QUERY_LAST_PATH) reports the path taken. */
     BP_OPT_PATH = 5,
     /* 1 (default): skip, per block of voxels, the projections whose footprint
@@ -96,14 +98,15 @@ typedef enum {
      * host-to-device copy per batch into a staging buffer, then a copy
      * kernel into the arrays. */
     BP_OPT_HOST_DIRECT = 7,
-    /* BP_F32 projections on the texture path: 1 (default) centre the detector
-     * coordinates per block of voxels and projection, 0 once per projection.
-     * Per-block centring costs a per-block pre-pass and 2 x 48 bytes of
-     * device memory per (block, projection of a batch) (768 MiB for a 512^3
-     * volume),
-     * and cuts the float32 rounding of u and v by the ratio of block to volume
-     * footprint (rel-L2 5e-7 instead of 1e-5 on a full 1248x960 detector).
-     * 16-bit storage and the TMA path always centre per projection. */
+    /* BP_F32 projections: 1 (default) centre the detector coordinates per
+     * block of voxels (the texture kernel's thread block, or the TMA path's
+     * 32x16x8 brick) and projection, 0 once per projection.  Per-block
+     * centring costs a pre-pass and 2 x 48 bytes of device memory per (block,
+     * projection of a batch) (768 MiB for a 512^3 volume on the texture path,
+     * 192 MiB on the TMA path), and cuts the float32 rounding of u and v by
+     * the ratio of block to volume footprint (rel-L2 5e-7 instead of 1e-5 on
+     * a full 1248x960 detector).  16-bit storage always centres per
+     * projection. */
     BP_OPT_BLOCK_CENTRE = 8
 } bp_option;
 

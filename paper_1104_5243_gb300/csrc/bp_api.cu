@@ -464,10 +464,12 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
     for (int c0 = 0; c0 < n; c0 += c->batch) {
         const int m = n - c0 < c->batch ? n - c0 : c->batch;
         const double *A0 = A + 12 * (size_t)c0;
-        // Automatic choice: the texture path with block culling (measured
-        // faster than the TMA path for every storage type on GB300); the TMA
-        // path only on request.
-        const bool tma = c->path == 2;
+        // Automatic choice, by measurement on GB300 (512^3 x 1248x960): the
+        // TMA path for float32 projections (the texture unit returns 32-bit
+        // gathers at half the 16-bit rate, which bounds the texture kernel;
+        // 1148 against 801 GUP/s), the texture path for 16-bit storage (1240
+        // against 1132).
+        const bool tma = c->path == 2 || (c->path == 0 && c->dtype == BP_F32);
         if (tma) {
             st = ensure_pairs(c);
             if (st != BP_OK)
@@ -510,15 +512,21 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 CTX_CK(c, launch_convert(cb, c->isx, c->isy, mode, c->copy_stream));
             }
         }
-        // Texture path: the batch's kernel parameters, and the per-block
-        // pre-pass (culling masks, centring records) on the copy stream: it
-        // needs only the matrices, so it overlaps the previous batch's
+        // The batch's kernel parameters, and the per-tile pre-pass on the copy
+        // stream: culling masks (texture path; the TMA producer culls per
+        // brick itself) and centring records (float32 projections).  It needs
+        // only the matrices, so it overlaps the previous batch's
         // backprojection; its buffers belong to this input set, which the
-        // copy stream has waited for.
+        // copy stream has waited for.  Tiles: the texture kernel's blocks or
+        // the TMA path's bricks.
         FwdBatch b;
         unsigned long long *masks = nullptr;
         float4 *centres = nullptr;
-        if (!tma) {
+        int tile[3] = {kBrickX, kBrickY, kBrickZ};
+        if (!tma)
+            fwd_tile(c->lanes_x, &tile[0], &tile[1], &tile[2]);
+        const long long nb = tile_count(c->L, tile[0], tile[1], tile[2]);
+        {
             b.n = m;
             double rows[kMaxBatch][3][4];   // the same centred rows in float64
             for (int j = 0; j < m; ++j) {
@@ -537,8 +545,7 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                     rows[j][2][q] = a[8 + q];
                 }
             }
-            const long long nb = fwd_blocks(c->L, c->lanes_x);
-            if (c->cull) {
+            if (c->cull && !tma) {
                 if (nb > c->mask_blocks[s]) {
                     if (c->masks[s])
                         CTX_CK(c, cudaFree(c->masks[s]));
@@ -548,7 +555,7 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                     c->mask_blocks[s] = nb;
                 }
                 masks = c->masks[s];
-            } else {
+            } else if (!tma) {
                 c->work_host += (unsigned long long)m * c->L * c->L * c->L;
             }
             CentreBatch cb;
@@ -564,8 +571,8 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 centres = c->centres[s];
                 centre_batch(&cb, &rows[0][0][0], m, c->O, c->R);
             }
-            CTX_CK(c, launch_block_prepass(b, centres ? &cb : nullptr, g, c->isx, c->isy, c->lanes_x, masks, centres,
-                                           masks ? c->work_dev : nullptr, c->copy_stream));
+            CTX_CK(c, launch_block_prepass(b, centres ? &cb : nullptr, g, c->isx, c->isy, tile[0], tile[1], tile[2],
+                                           masks, centres, masks ? c->work_dev : nullptr, c->copy_stream));
         }
         CTX_CK(c, cudaEventRecord(c->copy_done[s], c->copy_stream));
         CTX_CK(c, cudaStreamWaitEvent(c->stream, c->copy_done[s], 0));
@@ -590,6 +597,8 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 tb.map[j] = c->maps[s][j];
                 tb.img[j] = static_cast<const char *>(c->pairs[s]) + c->pair_slot_bytes * j;
             }
+            tb.centres = centres;
+            tb.bricks = nb;
             CTX_CK(c, launch_bp_tma(tb, c->vol, g, pair_kind(c), !c->vol_zero, c->ieee_rcp, c->err_dev, c->work_dev,
                                     c->stream));
         } else {

@@ -178,7 +178,7 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
 }
 
 // Block tile of a layout: (TX, TY, TZ) voxels.
-static void layout_tile(int lanes_x, int *tx, int *ty, int *tz)
+void fwd_tile(int lanes_x, int *tx, int *ty, int *tz)
 {
     int lx = 8, ly = 1, vpl = kVoxPerLane;
     switch (lanes_x) {
@@ -196,11 +196,16 @@ static void layout_tile(int lanes_x, int *tx, int *ty, int *tz)
     *tz = 32 / (lx * ly);
 }
 
+long long tile_count(int L, int tx, int ty, int tz)
+{
+    return (long long)((L + tx - 1) / tx) * ((L + ty - 1) / ty) * ((L + tz - 1) / tz);
+}
+
 long long fwd_blocks(int L, int lanes_x)
 {
     int tx, ty, tz;
-    layout_tile(lanes_x, &tx, &ty, &tz);
-    return (long long)((L + tx - 1) / tx) * ((L + ty - 1) / ty) * ((L + tz - 1) / tz);
+    fwd_tile(lanes_x, &tx, &ty, &tz);
+    return tile_count(L, tx, ty, tz);
 }
 
 template <int KIND, bool IEEE, int LX, int LY, int VPL = kVoxPerLane>
@@ -371,15 +376,13 @@ block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__
 }
 
 cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const VolGeom &g, int isx, int isy,
-                                 int lanes_x, unsigned long long *masks, float4 *centres,
+                                 int tx, int ty, int tz, unsigned long long *masks, float4 *centres,
                                  unsigned long long *work, cudaStream_t s)
 {
     if (b.n <= 0 || (!masks && !centres))
         return cudaSuccess;
-    int tx, ty, tz;
-    layout_tile(lanes_x, &tx, &ty, &tz);
     const int nbx = (g.L + tx - 1) / tx, nby = (g.L + ty - 1) / ty;
-    const long long nblocks = fwd_blocks(g.L, lanes_x);
+    const long long nblocks = tile_count(g.L, tx, ty, tz);
     const unsigned grid = (unsigned)((nblocks + 255) / 256);
     if (centres && cb) {
         block_prepass_kernel<true><<<grid, 256, 0, s>>>(b, *cb, g, isx, isy, tx, ty, tz, nbx, nby, nblocks, masks,

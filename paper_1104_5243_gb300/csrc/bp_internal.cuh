@@ -96,9 +96,13 @@ cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int t
 //   (every term of those updates is exactly zero);
 // - centres (if not NULL, with cb): the block centring records;
 // - work (if not NULL): the kept updates are added to *work.
+// The pre-pass works on any tile of voxels: the texture kernel's block
+// (fwd_tile of its layout) or the TMA path's brick.
+void fwd_tile(int lanes_x, int *tx, int *ty, int *tz);
 long long fwd_blocks(int L, int lanes_x);
+long long tile_count(int L, int tx, int ty, int tz);
 cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const VolGeom &g, int isx, int isy,
-                                 int lanes_x, unsigned long long *masks, float4 *centres,
+                                 int tx, int ty, int tz, unsigned long long *masks, float4 *centres,
                                  unsigned long long *work, cudaStream_t s);
 
 // smem: accumulate each block's footprint in shared memory (kAdjTile pixels
@@ -108,32 +112,37 @@ cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom
                               float *out, int isx, int isy, bool ieee_rcp, bool smem, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
-// TMA / shared-memory path (bp_tma.cu).  Bricks of 16 x 8 x 8 voxels per
-// 256-thread block; projections staged as "pair images" (element c of a row
-// holds pixels c-1 and c) and loaded per brick and projection as one TMA box
-// of BU pair columns by BV rows.
-constexpr int kBrickX = 16, kBrickY = 8, kBrickZ = 8;
+// TMA / shared-memory path (bp_tma.cu).  Bricks of 32 x 16 x 8 voxels per
+// block of 256 consumer threads (16 voxels each) and one producer warp;
+// projections staged as "pair images" (element c of a row holds pixels c-1
+// and c) and loaded per brick and projection as one TMA box of BU pair
+// columns by BV rows.  A box of that size holds the footprint of 97 % of the
+// visible (brick, projection) pairs of the 512^3 C-arm scan; larger
+// footprints (bricks near the source) read the pair image from global memory.
+constexpr int kBrickX = 32, kBrickY = 16, kBrickZ = 8;
 enum PairKind { kPairF32 = 0, kPairF16 = 1, kPairBF16 = 2 };
 template <int KIND> struct TmaBox;
-// Row pitches of 528 B (f32 pairs) and 272 B (16-bit pairs) put successive
-// box rows 4 banks apart, so lanes on the same column in different rows do
-// not conflict.
-template <> struct TmaBox<kPairF32> { static constexpr int BU = 66, BV = 32; };
-template <> struct TmaBox<kPairF16> { static constexpr int BU = 68, BV = 32; };
-template <> struct TmaBox<kPairBF16> { static constexpr int BU = 68, BV = 32; };
+// Row pitches of 228 words (f32 pairs) and 100 words (16-bit pairs), both
+// 4 modulo 32, put successive box rows 4 banks apart, so lanes on the same
+// column in different rows do not conflict.
+template <> struct TmaBox<kPairF32> { static constexpr int BU = 114, BV = 32, S = 2; };
+template <> struct TmaBox<kPairF16> { static constexpr int BU = 100, BV = 32, S = 3; };
+template <> struct TmaBox<kPairBF16> { static constexpr int BU = 100, BV = 32, S = 3; };
 // 32-bit words per pair, and the pair-column alignment that keeps the TMA
 // box origin on a 16-byte boundary.
 template <int KIND> constexpr int kPairWords = KIND == kPairF32 ? 2 : 1;
 template <int KIND> constexpr int kPairAlign = KIND == kPairF32 ? 2 : 4;
 constexpr int kTmaWaitIters = 1 << 14;          // bounded waits: at most ~2 s
 constexpr unsigned kTmaSuspendNs = 100000;        // suspend hint per try, ns
-constexpr int kTmaStages = 3;                     // depth of the shared-memory ring
+constexpr int kTmaMaxStages = 3;                  // deepest shared-memory ring (S above)
 
 struct TmaBatch {
     CUtensorMap map[kMaxBatch];        // one per projection's pair image
     float4 m[kMaxBatch][3];            // rows as in FwdBatch (centred, +1 folded)
     int2 k[kMaxBatch];                 // integer centring offsets (ku, kv)
     const void *img[kMaxBatch];        // pair image base, for the global path
+    const float4 *centres;             // per-brick centring records (NULL: per projection)
+    long long bricks;                  // bricks of the volume (record plane stride)
     int n, isx, isy, pitch;            // pitch: pair elements per row
 };
 

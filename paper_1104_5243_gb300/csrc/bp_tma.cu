@@ -4,7 +4,7 @@
 //
 // Why: the texture unit returns 2x2 gathers of 32-bit texels at half the
 // rate of 16-bit ones, which bounds the float32 form of the texture kernel.
-// Here each block owns a 16 x 8 x 8 voxel brick; for every projection a
+// Here each block owns a 32 x 16 x 8 voxel brick; for every projection a
 // producer warp projects the brick's 8 corners (one lane each), and either
 //   * culls the projection when the footprint misses the detector (every
 //     term is then exactly zero -- the line-wise clipping of Sect. 3.3 at
@@ -96,9 +96,27 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 // Integer value of an integer-valued float with |f| < 2^22, without the
 // float-to-int conversion unit: adding 1.5 * 2^23 puts the integer in the
 // low mantissa bits.
+constexpr float kIntMagic = 12582912.0f;
+constexpr uint32_t kIntMagicBits = 0x4B400000u;
 __device__ __forceinline__ int int_of_integral(float f)
 {
-    return __float_as_int(f + 12582912.0f) - 0x4B400000;
+    return __float_as_int(f + kIntMagic) - (int)kIntMagicBits;
+}
+
+// Shared-memory loads at a 32-bit shared address plus a constant offset.
+template <int OFF>
+__device__ __forceinline__ float2 lds_f2(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(a), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ unsigned int lds_u32(uint32_t a)
+{
+    unsigned int v;
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+    return v;
 }
 
 // The four corners of an update from two pair loads.  Pair = (left, right).
@@ -109,6 +127,8 @@ template <>
 struct Pairs<kPairF32> {
     using T = float2;
     __device__ static float2 unpack(float2 p) { return p; }
+    template <int OFF>
+    __device__ static float2 load(uint32_t a) { return lds_f2<OFF>(a); }
 };
 
 template <>
@@ -118,6 +138,8 @@ struct Pairs<kPairF16> {
     {
         return __half22float2(*reinterpret_cast<const __half2 *>(&p));
     }
+    template <int OFF>
+    __device__ static float2 load(uint32_t a) { return unpack(lds_u32<OFF>(a)); }
 };
 
 template <>
@@ -127,6 +149,8 @@ struct Pairs<kPairBF16> {
     {
         return make_float2(__uint_as_float(p << 16), __uint_as_float(p & 0xffff0000u));
     }
+    template <int OFF>
+    __device__ static float2 load(uint32_t a) { return unpack(lds_u32<OFF>(a)); }
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -134,43 +158,54 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// The 4 updates of one consumer lane for projection i, reading the corner
-// pairs from the staged tile (SMEM) or from the global pair image; the two
-// forms are separate loop bodies so neither carries the other's work.
+// The 16 updates of one consumer lane for projection i (matrix rows ru, rv,
+// rw), reading the corner pairs from the staged tile (SMEM) or from the
+// global pair image; the two forms are separate loop bodies so neither
+// carries the other's work.  Lane voxels: X[kx] (kx = 0..3, 8 apart), Y[ky]
+// (8 apart), Z[kz] (4 apart); absolute, or offsets from the brick centre
+// with per-brick centring.
 template <int KIND, bool IEEE, bool SMEM>
-__device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, int cu, int cv,
-                                            const typename Pairs<KIND>::T *tile, const float (&Xv)[2], float Y,
-                                            const float (&Zv)[2], float (&acc)[4])
+__device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const float4 ru, const float4 rv,
+                                            const float4 rw, int4 mt, uint32_t tile, const float (&X)[4],
+                                            const float (&Y)[2], const float (&Z)[2], float (&acc)[16])
 {
     using P = Pairs<KIND>;
     using T = typename P::T;
-    constexpr int BU = TmaBox<KIND>::BU, kBufElems = BU * TmaBox<KIND>::BV;
-    const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+    constexpr int BU = TmaBox<KIND>::BU;
+    // SMEM: mt.y holds the bits of off = (row offset) * BU + (column offset)
+    // + 1.5 * 2^23, so fv0 * BU + fu0 + off is the element index of the top
+    // pair in the staged box, plus the magic, exactly (all integers far below
+    // 2^22); its bits times the pair size, plus (tile - magic bits * pair
+    // size) modulo 2^32, are the shared address.
+    const float off = __int_as_float(mt.y);
+    const uint32_t base = tile - kIntMagicBits * (uint32_t)sizeof(T);
 #pragma unroll
-    for (int kz = 0; kz < 2; ++kz) {
-        const float bu = fmaf(ru.y, Y, fmaf(ru.z, Zv[kz], ru.w));
-        const float bv = fmaf(rv.y, Y, fmaf(rv.z, Zv[kz], rv.w));
-        const float bw = fmaf(rw.y, Y, fmaf(rw.z, Zv[kz], rw.w));
+    for (int q = 0; q < 4; ++q) {
+        const int ky = q >> 1, kz = q & 1;
+        const float bu = fmaf(ru.y, Y[ky], fmaf(ru.z, Z[kz], ru.w));
+        const float bv = fmaf(rv.y, Y[ky], fmaf(rv.z, Z[kz], rv.w));
+        const float bw = fmaf(rw.y, Y[ky], fmaf(rw.z, Z[kz], rw.w));
 #pragma unroll
-        for (int kx = 0; kx < 2; ++kx) {
-            const float uw = fmaf(ru.x, Xv[kx], bu);
-            const float vw = fmaf(rv.x, Xv[kx], bv);
-            const float w = fmaf(rw.x, Xv[kx], bw);
+        for (int kx = 0; kx < 4; ++kx) {
+            const float uw = fmaf(ru.x, X[kx], bu);
+            const float vw = fmaf(rv.x, X[kx], bv);
+            const float w = fmaf(rw.x, X[kx], bw);
             const float r = recip_tma<IEEE>(w);
             const float u = uw * r, v = vw * r;
             const float fu0 = floorf(u), fv0 = floorf(v);
-            const int col = int_of_integral(fu0) + cu;
-            const int row = int_of_integral(fv0) + cv;
             float2 top, bot;
             if constexpr (SMEM) {
-                // the corner-based box covers every voxel of the volume with a
-                // pixel of margin; the clamp only guards the array for lanes
-                // beyond a ragged edge
-                const int idx = (int)min((unsigned)(row * BU + col), (unsigned)(kBufElems - BU - 1));
-                top = P::unpack(tile[idx]);
-                bot = P::unpack(tile[idx + BU]);
+                // every lane's coordinates lie in the volume (clamped at
+                // setup) and the box covers the brick's footprint with a pixel
+                // of margin, so the address is inside the staged box
+                const float e = fmaf(fv0, (float)BU, fu0 + off);
+                const uint32_t a = (uint32_t)__float_as_int(e) * (uint32_t)sizeof(T) + base;
+                top = P::template load<0>(a);
+                bot = P::template load<BU * (int)sizeof(T)>(a);
             } else {
                 // rows outside the detector are zero
+                const int col = int_of_integral(fu0) + mt.z;
+                const int row = int_of_integral(fv0) + mt.w;
                 const T *img = reinterpret_cast<const T *>(b.img[i]);
                 const bool cok = col >= 0 && col <= b.isx;
                 const T *p = img + (long long)row * b.pitch + col;
@@ -182,18 +217,22 @@ __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, int cu, in
             const float t = fmaf(fu, top.y - top.x, top.x);
             const float bt = fmaf(fu, bot.y - bot.x, bot.x);
             const float fx = fmaf(fv, bt - t, t);
-            acc[kz * 2 + kx] = fmaf(fx, r * r, acc[kz * 2 + kx]);
+            acc[q * 4 + kx] = fmaf(fx, r * r, acc[q * 4 + kx]);
         }
     }
 }
 
-// Warp-specialised pipeline: warps 0..7 compute (256 consumer threads, 4
-// voxels each), warp 8 is the producer.  Stage s of the kTmaStages-deep ring
+// Warp-specialised pipeline: warps 0..7 compute (256 consumer threads, 16
+// voxels each), warp 8 is the producer.  Stage s of the S-deep ring
 // has a "full" barrier (the producer's arrival, plus the TMA bytes when a
 // tile is loaded) and an "empty" barrier (one arrival per consumer warp when
 // it is done with the stage).  No block-wide barrier inside the loop.
-template <int KIND, bool IEEE>
-__global__ void __launch_bounds__(kThreads + 32, 4)
+// BLK: per-brick centring; the producer copies the brick's centring records
+// (u row, v row, (w_c, ku_b, kv_b)) of each projection into the stage, and
+// consumers work with offsets from the brick centre, as the texture kernel
+// does per block.
+template <int KIND, bool IEEE, bool BLK>
+__global__ void __launch_bounds__(kThreads + 32, 3)
 bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const VolGeom g, int accumulate,
               int *__restrict__ err, unsigned long long *__restrict__ work)
 {
@@ -201,20 +240,23 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     using T = typename P::T;
     constexpr int BU = TmaBox<KIND>::BU, BV = TmaBox<KIND>::BV;
     constexpr int kBufElems = BU * BV;
-    constexpr int S = kTmaStages;
+    constexpr int S = TmaBox<KIND>::S;
     constexpr int kConsumerWarps = kThreads / 32;
     extern __shared__ __align__(128) unsigned char dyn_smem[];   // the ring: S stages of kBufElems pairs
     T (*buf)[kBufElems] = reinterpret_cast<T (*)[kBufElems]>(dyn_smem);
     __shared__ __align__(8) uint64_t full[S], empty[S];
-    // per stage: mode (0 culled, 1 shared memory, 2 global) and the column /
-    // row offsets that turn floor(u'), floor(v') into indices of the staged
-    // box (mode 1) or of the global pair image (mode 2)
+    // per stage: mode (0 culled, 1 shared memory, 2 global), the element
+    // offset of the staged box as float bits (mode 1), and the column / row
+    // offsets that turn floor(u'), floor(v') into indices of the global pair
+    // image (mode 2)
     __shared__ int4 meta[S];
+    __shared__ float4 rec[BLK ? S : 1][3];
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = g.L;
     const int bx0 = blockIdx.x * kBrickX, by0 = blockIdx.y * kBrickY, bz0 = blockIdx.z * kBrickZ;
+    const size_t brick = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < S; ++q) {
@@ -262,6 +304,19 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
             }
             if (lane == 0) {
                 const int2 kc = b.k[i];
+                // offsets the consumers' floor(u'), floor(v') are relative to:
+                // the projection's, or with BLK the brick's (the box itself
+                // does not depend on the centring)
+                int2 kb = kc;
+                if constexpr (BLK) {
+                    const size_t plane = (size_t)kMaxBatch * b.bricks;
+                    const float4 *cr = b.centres + (size_t)i * b.bricks + brick;
+                    rec[st][0] = cr[0];
+                    rec[st][1] = cr[plane];
+                    const float4 cw = cr[2 * plane];
+                    rec[st][2] = cw;
+                    kb = make_int2((int)cw.y, (int)cw.z);
+                }
                 umin = fminf(fmaxf(umin, -1.0e6f), 1.0e6f);   // keep the int conversions in range
                 umax = fminf(fmaxf(umax, -1.0e6f), 1.0e6f);
                 vmin = fminf(fmaxf(vmin, -1.0e6f), 1.0e6f);
@@ -280,7 +335,8 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                     if (mode == 2)
                         cx0 = ry0 = 0;   // the global path indexes the whole pair image
                 }
-                meta[st] = make_int4(mode, kc.x - cx0, kc.y - 1 - ry0, 0);
+                const int cu = kb.x - cx0, cv = kb.y - 1 - ry0;
+                meta[st] = make_int4(mode, __float_as_int((float)(cv * BU + cu) + kIntMagic), cu, cv);
                 computed += mode != 0;
                 if (mode == 1) {
                     mbar_expect_tx(&full[st], (uint32_t)(kBufElems * sizeof(T)));   // also publishes meta
@@ -307,18 +363,39 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
 
     // ---------------- consumers
     const int tx = lane & 7, tz = lane >> 3;
-    // this lane's voxels: x0 + {0, 8}, y, z0 + {0, 4}
-    const int x0 = bx0 + tx, y = by0 + warp, z0 = bz0 + tz;
-    const float Xv[2] = {fmaf(g.R, (float)x0, g.Ox), fmaf(g.R, (float)(x0 + 8), g.Ox)};
-    const float Y = fmaf(g.R, (float)y, g.Oy);
-    const float Zv[2] = {fmaf(g.R, (float)z0, g.Oz), fmaf(g.R, (float)(z0 + 4), g.Oz)};
+    // this lane's voxels: x0 + {0, 8, 16, 24}, y0 + {0, 8}, z0 + {0, 4};
+    // lanes beyond a ragged edge compute with the last voxel's coordinates
+    // (inside the brick box, so their loads stay in the staged tile) and
+    // store nothing
+    // (BLK: offsets from the centre of the brick's voxel box clipped to the
+    // volume, (x0 + x1) / 2 etc., a multiple of 1/2, as in the pre-pass)
+    const int x0 = bx0 + tx, y0 = by0 + warp, z0 = bz0 + tz;
+    const float hx = 0.5f * (float)(bx0 + min(bx0 + kBrickX, L) - 1);
+    const float hy = 0.5f * (float)(by0 + min(by0 + kBrickY, L) - 1);
+    const float hz = 0.5f * (float)(bz0 + min(bz0 + kBrickZ, L) - 1);
+    float X[4], Y[2], Z[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int x = min(x0 + 8 * k, L - 1);
+        X[k] = BLK ? g.R * ((float)x - hx) : fmaf(g.R, (float)x, g.Ox);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int y = min(y0 + 8 * k, L - 1), z = min(z0 + 4 * k, L - 1);
+        Y[k] = BLK ? g.R * ((float)y - hy) : fmaf(g.R, (float)y, g.Oy);
+        Z[k] = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)z, g.Oz);
+    }
 
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        acc[k] = 0.f;
     bool ok = true;
+    int s = 0;
+    uint32_t phase = 0;
 #pragma unroll 1
     for (int i = 0; i < b.n; ++i) {
-        const int s = i % S;
-        if (!mbar_wait_bounded(&full[s], (i / S) & 1)) {
+        if (!mbar_wait_bounded(&full[s], phase)) {
             if (lane == 0) {
                 atomicExch(&abort_flag, 1);
                 atomicExch(err, 1);
@@ -327,48 +404,75 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
             break;
         }
         const int4 mt = meta[s];
-        const int mode = mt.x;
-        if (mode == 1)        // tile in shared memory (the common case)
-            tma_updates<KIND, IEEE, true>(b, i, mt.y, mt.z, buf[s], Xv, Y, Zv, acc);
-        else if (mode == 2)   // footprint larger than the tile
-            tma_updates<KIND, IEEE, false>(b, i, mt.y, mt.z, buf[s], Xv, Y, Zv, acc);
+        if (mt.x != 0) {
+            float4 ru, rv, rw = b.m[i][2];
+            if constexpr (BLK) {
+                ru = rec[s][0];
+                rv = rec[s][1];
+                rw.w = rec[s][2].x;
+            } else {
+                ru = b.m[i][0];
+                rv = b.m[i][1];
+            }
+            if (mt.x == 1)   // tile in shared memory (the common case)
+                tma_updates<KIND, IEEE, true>(b, i, ru, rv, rw, mt, smem_u32(buf[s]), X, Y, Z, acc);
+            else             // footprint larger than the tile
+                tma_updates<KIND, IEEE, false>(b, i, ru, rv, rw, mt, 0u, X, Y, Z, acc);
+        }
         __syncwarp();
         if (lane == 0)
             mbar_arrive(&empty[s]);   // this warp is done with stage s
+        if (++s == S) {
+            s = 0;
+            phase ^= 1u;
+        }
     }
 
-    if (!ok || y >= L)
+    if (!ok)
         return;
 #pragma unroll
-    for (int kz = 0; kz < 2; ++kz) {
-        const int z = z0 + 4 * kz;
-        if (z >= L)
+    for (int q = 0; q < 4; ++q) {
+        const int y = y0 + 8 * (q >> 1), z = z0 + 4 * (q & 1);
+        if (y >= L || z >= L)
             continue;
         float *row = vol + ((size_t)z * L + y) * L;
 #pragma unroll
-        for (int kx = 0; kx < 2; ++kx) {
+        for (int kx = 0; kx < 4; ++kx) {
             const int x = x0 + 8 * kx;
             if (x < L)
-                row[x] = (accumulate ? row[x] : 0.f) + acc[kz * 2 + kx];
+                row[x] = (accumulate ? row[x] : 0.f) + acc[q * 4 + kx];
         }
     }
 }
 
+template <int KIND, bool IEEE, bool BLK>
+static cudaError_t launch_tma_blk(const TmaBatch &b, float *vol, const VolGeom &g, bool acc, int *err,
+                                  unsigned long long *work, cudaStream_t s)
+{
+    dim3 grid((g.L + kBrickX - 1) / kBrickX, (g.L + kBrickY - 1) / kBrickY, (g.L + kBrickZ - 1) / kBrickZ);
+    using T = typename Pairs<KIND>::T;
+    const size_t smem = sizeof(T) * TmaBox<KIND>::BU * TmaBox<KIND>::BV * TmaBox<KIND>::S;
+    // the ring exceeds the 48 KB default for float32 pairs (set per call:
+    // cheap, and correct on whichever device is current)
+    cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<KIND, IEEE, BLK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    bp_tma_kernel<KIND, IEEE, BLK><<<grid, kThreads + 32, smem, s>>>(b, vol, g, acc ? 1 : 0, err, work);
+    return cudaGetLastError();
+}
+
+// Per-brick centring exists for the float32 pairs only (16-bit storage
+// rounds far above the coordinate error it removes).
 template <int KIND, bool IEEE>
 static cudaError_t launch_tma_kind(const TmaBatch &b, float *vol, const VolGeom &g, bool acc, int *err,
                                    unsigned long long *work, cudaStream_t s)
 {
-    dim3 grid((g.L + kBrickX - 1) / kBrickX, (g.L + kBrickY - 1) / kBrickY, (g.L + kBrickZ - 1) / kBrickZ);
-    using T = typename Pairs<KIND>::T;
-    const size_t smem = sizeof(T) * TmaBox<KIND>::BU * TmaBox<KIND>::BV * kTmaStages;
-    // the ring exceeds the 48 KB default for float32 pairs (set per call:
-    // cheap, and correct on whichever device is current)
-    cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<KIND, IEEE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    bp_tma_kernel<KIND, IEEE><<<grid, kThreads + 32, smem, s>>>(b, vol, g, acc ? 1 : 0, err, work);
-    return cudaGetLastError();
+    if constexpr (KIND == kPairF32) {
+        if (b.centres)
+            return launch_tma_blk<KIND, IEEE, true>(b, vol, g, acc, err, work, s);
+    }
+    return launch_tma_blk<KIND, IEEE, false>(b, vol, g, acc, err, work, s);
 }
 
 cudaError_t launch_bp_tma(const TmaBatch &b, float *vol, const VolGeom &g, int pair_kind, bool accumulate,

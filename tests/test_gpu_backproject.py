@@ -185,8 +185,9 @@ def test_full_size_sampled_voxels(L, dtype, tol):
     bp.close()
 
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("dtype,tol", [("f32", FP32_TOL), ("f16", FP16_TOL)])
-def test_full_detector_ramp_filtered_phantom(dtype, tol):
+def test_full_detector_ramp_filtered_phantom(dtype, tol, path):
     """512^3 with the full 1248x960 detector and a ramp-filtered 50-ellipsoid
     phantom (seed 2), every 16th of the 496 projections (the oracle computes
     the line integrals, the FDK filtering and 4096 sampled voxels)."""
@@ -211,12 +212,13 @@ def test_full_detector_ramp_filtered_phantom(dtype, tol):
     for centre in ((1, 0) if dtype == "f32" else (1,)):
         bp = api.Backprojector(vol.L, vol.R, vol.O, full.isx, full.isy, dtype=dtype)
         bp.set_option(N.BP_OPT_BLOCK_CENTRE, centre)
+        bp.set_option(N.BP_OPT_PATH, path)
         bp.add_projections(torch.from_numpy(q).cuda(), A)
         got = bp.finalize().view(-1)
         bp.close()
         g = got[torch.from_numpy(idx).cuda()].cpu().numpy()
         errs[centre] = rel_l2(g, ref)
-        print(f"512^3 phantom {dtype} block_centre={centre} sampled rel-L2 {errs[centre]:.3e} "
+        print(f"512^3 phantom {dtype} path={path} block_centre={centre} sampled rel-L2 {errs[centre]:.3e} "
               f"max-abs {np.abs(g - ref).max():.3e}")
     assert errs[1] <= tol
     if dtype == "f32":
@@ -230,9 +232,10 @@ def test_full_detector_ramp_filtered_phantom(dtype, tol):
 # per-projection centring, so the volumes agree bit for bit (culled bricks
 # only skip exact zeros).
 def run_path(vol, scan, A, q, path, dtype="f32", block_centre=None):
-    """block_centre=None keeps the default; the TMA path always centres per
-    projection, so bit-identity with it needs block_centre=0 on the texture
-    path for float32 projections."""
+    """block_centre=None keeps the default (per-block centring for float32
+    projections, with the texture kernel's blocks or the TMA path's bricks as
+    the blocks); bit-identity between the paths needs block_centre=0 on both
+    for float32 projections."""
     api = native()
     from paper_1104_5243_gb300 import _native as N
     bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype)
@@ -250,16 +253,17 @@ def run_path(vol, scan, A, q, path, dtype="f32", block_centre=None):
 def test_tma_path_is_bit_identical_to_texture_path(dtype):
     scan, vol, A, ell, q, ref = tiny_phantom_case()
     tex, p1 = run_path(vol, scan, A, q, 1, dtype, block_centre=0)
-    tma, p2 = run_path(vol, scan, A, q, 2, dtype)
+    tma, p2 = run_path(vol, scan, A, q, 2, dtype, block_centre=0)
     assert (p1, p2) == ("texture", "tma")
     assert torch.equal(tex, tma)
     tol = {"f32": FP32_TOL, "f16": FP16_TOL, "bf16": BF16_TOL}[dtype]
     assert rel_l2(tma.numpy(), ref) <= tol
-    # the default texture path (per-block centring for float32) matches too
-    blk, _ = run_path(vol, scan, A, q, 1, dtype)
-    assert rel_l2(blk.numpy(), ref) <= tol
-    if dtype != "f32":
-        assert torch.equal(blk, tex)
+    # the defaults (per-block centring for float32) match the oracle too
+    for path in (1, 2):
+        blk, _ = run_path(vol, scan, A, q, path, dtype)
+        assert rel_l2(blk.numpy(), ref) <= tol
+        if dtype != "f32":
+            assert torch.equal(blk, tex)
 
 
 @pytest.mark.parametrize("L,isx,isy,n", [(37, 53, 41, 70), (1, 7, 5, 3), (40, 24, 10, 20)])
@@ -270,11 +274,12 @@ def test_tma_path_ragged_and_partial_detector(L, isx, isy, n):
     q = np.random.default_rng(L + n).standard_normal((n, isy, isx)).astype(np.float32)
     ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
     tex, _ = run_path(vol, scan, A, q, 1, block_centre=0)
-    tma, _ = run_path(vol, scan, A, q, 2)
+    tma, _ = run_path(vol, scan, A, q, 2, block_centre=0)
     assert torch.equal(tex, tma)
     assert rel_l2(tma.numpy(), ref) <= FP32_TOL
-    blk, _ = run_path(vol, scan, A, q, 1)
-    assert rel_l2(blk.numpy(), ref) <= FP32_TOL
+    for path in (1, 2):
+        blk, _ = run_path(vol, scan, A, q, path)
+        assert rel_l2(blk.numpy(), ref) <= FP32_TOL
 
 
 def test_tma_global_fallback_when_footprints_exceed_the_tile():
@@ -286,23 +291,26 @@ def test_tma_global_fallback_when_footprints_exceed_the_tile():
     A = oracle.carm_matrices(scan)
     q = synth.uniform_stack(scan.n, scan.isy, scan.isx, seed=11)
     tex, _ = run_path(vol, scan, A, q, 1, block_centre=0)
-    tma, _ = run_path(vol, scan, A, q, 2)
+    tma, _ = run_path(vol, scan, A, q, 2, block_centre=0)
     assert torch.equal(tex, tma)
     idx = np.random.default_rng(1).integers(0, 256 ** 3, size=512)
     ref = oracle.backproject_voxels(vol.L, vol.R, vol.O, q, A, idx)
     assert rel_l2(tma.view(-1).numpy()[idx], ref) <= FP32_TOL
+    blk, _ = run_path(vol, scan, A, q, 2)
+    assert rel_l2(blk.view(-1).numpy()[idx], ref) <= FP32_TOL
 
 
-def test_automatic_path_choice():
+@pytest.mark.parametrize("dtype,expect", [("f32", "tma"), ("f16", "texture"), ("bf16", "texture")])
+def test_automatic_path_choice(dtype, expect):
+    """Automatic: the TMA path for float32 projections, the texture path for
+    16-bit storage (the faster of the two for each on GB300)."""
     scan = synth.SCANS["full"]
     A = oracle.carm_matrices(scan)[:8]
     q = synth.uniform_stack(8, scan.isy, scan.isx, seed=3)
-    auto, p_auto = run_path(synth.Volume(128), scan, A, q, 0)
-    tex, p_tex = run_path(synth.Volume(128), scan, A, q, 1)
-    tma, p_tma = run_path(synth.Volume(128), scan, A, q, 2)
-    assert (p_auto, p_tex, p_tma) == ("texture", "texture", "tma")
-    assert torch.equal(auto, tex)
-    assert rel_l2(auto.numpy(), tma.numpy()) <= FP32_TOL
+    auto, p_auto = run_path(synth.Volume(128), scan, A, q, 0, dtype)
+    forced, p_forced = run_path(synth.Volume(128), scan, A, q, 2 if expect == "tma" else 1, dtype)
+    assert (p_auto, p_forced) == (expect, expect)
+    assert torch.equal(auto, forced)
 
 
 def test_reciprocal_modes_accuracy_table():
