@@ -227,10 +227,10 @@ __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const floa
 // has a "full" barrier (the producer's arrival, plus the TMA bytes when a
 // tile is loaded) and an "empty" barrier (one arrival per consumer warp when
 // it is done with the stage).  No block-wide barrier inside the loop.
-// BLK: per-brick centring; the producer copies the brick's centring records
-// (u row, v row, (w_c, ku_b, kv_b)) of each projection into the stage, and
-// consumers work with offsets from the brick centre, as the texture kernel
-// does per block.
+// BLK: per-brick centring; the block stages the brick's centring records
+// (u row, v row, (w_c, ku_b, kv_b)) of every projection in shared memory at
+// the start, and consumers work with offsets from the brick centre, as the
+// texture kernel does per block.
 template <int KIND, bool IEEE, bool BLK>
 __global__ void __launch_bounds__(kThreads + 32, 3)
 bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const VolGeom g, int accumulate,
@@ -250,7 +250,9 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     // offsets that turn floor(u'), floor(v') into indices of the global pair
     // image (mode 2)
     __shared__ int4 meta[S];
-    __shared__ float4 rec[BLK ? S : 1][3];
+    // BLK: the brick's centring records of every projection of the batch
+    // (u row, v row, (w_c, ku_b, kv_b)), staged once
+    __shared__ float4 rec[3][BLK ? kMaxBatch : 1];
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -265,6 +267,13 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
+    }
+    if constexpr (BLK) {
+        if (threadIdx.x < 3 * kMaxBatch) {
+            const int part = threadIdx.x / kMaxBatch, i = threadIdx.x % kMaxBatch;
+            if (i < b.n)
+                rec[part][i] = b.centres[((size_t)part * kMaxBatch + i) * b.bricks + brick];
+        }
     }
     __syncthreads();
 
@@ -291,7 +300,9 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                 break;
             const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
             const float w = fmaf(rw.x, X, fmaf(rw.y, Yc, fmaf(rw.z, Z, rw.w)));
-            const float r = 1.0f / w;
+            // the box has a pixel of margin: the approximate reciprocal (about
+            // 1 ulp) is far more accurate than the corners need
+            const float r = recip_tma<false>(w);
             const float u = fmaf(ru.x, X, fmaf(ru.y, Yc, fmaf(ru.z, Z, ru.w))) * r;
             const float v = fmaf(rv.x, X, fmaf(rv.y, Yc, fmaf(rv.z, Z, rv.w))) * r;
             float umin = u, umax = u, vmin = v, vmax = v;
@@ -308,15 +319,8 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                 // the projection's, or with BLK the brick's (the box itself
                 // does not depend on the centring)
                 int2 kb = kc;
-                if constexpr (BLK) {
-                    const size_t plane = (size_t)kMaxBatch * b.bricks;
-                    const float4 *cr = b.centres + (size_t)i * b.bricks + brick;
-                    rec[st][0] = cr[0];
-                    rec[st][1] = cr[plane];
-                    const float4 cw = cr[2 * plane];
-                    rec[st][2] = cw;
-                    kb = make_int2((int)cw.y, (int)cw.z);
-                }
+                if constexpr (BLK)
+                    kb = make_int2((int)rec[2][i].y, (int)rec[2][i].z);
                 umin = fminf(fmaxf(umin, -1.0e6f), 1.0e6f);   // keep the int conversions in range
                 umax = fminf(fmaxf(umax, -1.0e6f), 1.0e6f);
                 vmin = fminf(fmaxf(vmin, -1.0e6f), 1.0e6f);
@@ -407,9 +411,9 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
         if (mt.x != 0) {
             float4 ru, rv, rw = b.m[i][2];
             if constexpr (BLK) {
-                ru = rec[s][0];
-                rv = rec[s][1];
-                rw.w = rec[s][2].x;
+                ru = rec[0][i];
+                rv = rec[1][i];
+                rw.w = rec[2][i].x;
             } else {
                 ru = b.m[i][0];
                 rv = b.m[i][1];
