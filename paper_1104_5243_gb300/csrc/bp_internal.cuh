@@ -115,7 +115,8 @@ cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom
 // TMA / shared-memory path (bp_tma.cu).  Bricks of 32 x 16 x 8 voxels per
 // block of 256 consumer threads (16 voxels each) and one producer warp;
 // projections staged as "pair images" (element c of a row holds pixels c-1
-// and c) and loaded per brick and projection as one TMA box of BU pair
+// and c; for float32, pixel c-1 and the difference of c and c-1) and loaded
+// per brick and projection as one TMA box of BU pair
 // columns by BV rows.  A box of that size holds the footprint of 97 % of the
 // visible (brick, projection) pairs of the 512^3 C-arm scan; larger
 // footprints (bricks near the source) read the pair image from global memory.

@@ -17,7 +17,10 @@
 //     bounds-checked global-memory path.
 // The pair image stores element c = (p[c-1], p[c]) of each row (zero outside
 // the detector), so the four corners of an update are two shared-memory
-// loads: (tl, tr) from row iv and (bl, br) from row iv+1.
+// loads: (tl, tr) from row iv and (bl, br) from row iv+1.  Float32 pairs
+// hold (p[c-1], p[c] - p[c-1]) instead: the difference is the float32
+// subtraction the horizontal interpolation needs anyway (the texture kernel
+// computes the same one), done once per pixel instead of once per update.
 //
 // The coordinates, fractions and interpolation are computed exactly as in
 // the texture kernel, so both paths give bit-identical volumes.
@@ -126,6 +129,7 @@ struct Pairs;
 template <>
 struct Pairs<kPairF32> {
     using T = float2;
+    static constexpr bool kDiff = true;   // (left, right - left)
     __device__ static float2 unpack(float2 p) { return p; }
     template <int OFF>
     __device__ static float2 load(uint32_t a) { return lds_f2<OFF>(a); }
@@ -134,6 +138,7 @@ struct Pairs<kPairF32> {
 template <>
 struct Pairs<kPairF16> {
     using T = unsigned int;
+    static constexpr bool kDiff = false;
     __device__ static float2 unpack(unsigned int p)
     {
         return __half22float2(*reinterpret_cast<const __half2 *>(&p));
@@ -145,6 +150,7 @@ struct Pairs<kPairF16> {
 template <>
 struct Pairs<kPairBF16> {
     using T = unsigned int;
+    static constexpr bool kDiff = false;
     __device__ static float2 unpack(unsigned int p)
     {
         return make_float2(__uint_as_float(p << 16), __uint_as_float(p & 0xffff0000u));
@@ -214,8 +220,10 @@ __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const floa
                 bot = P::unpack(cok && row + 1 >= 0 && row + 1 < b.isy ? p[b.pitch] : zero);
             }
             const float fu = u - fu0, fv = v - fv0;
-            const float t = fmaf(fu, top.y - top.x, top.x);
-            const float bt = fmaf(fu, bot.y - bot.x, bot.x);
+            const float dt = P::kDiff ? top.y : top.y - top.x;
+            const float db = P::kDiff ? bot.y : bot.y - bot.x;
+            const float t = fmaf(fu, dt, top.x);
+            const float bt = fmaf(fu, db, bot.x);
             const float fx = fmaf(fv, bt - t, t);
             acc[q * 4 + kx] = fmaf(fx, r * r, acc[q * 4 + kx]);
         }
@@ -499,8 +507,9 @@ cudaError_t launch_bp_tma(const TmaBatch &b, float *vol, const VolGeom &g, int p
 
 // ---------------------------------------------------------------------------
 // Pair images: element c of row k holds (p[k][c-1], p[k][c]) for
-// c = 0 .. isx (zero outside the detector), in the storage type; elements
-// c > isx of the padded row are zero.  One thread per element.
+// c = 0 .. isx (zero outside the detector), in the storage type, or for
+// float32 (p[k][c-1], p[k][c] - p[k][c-1]); elements c > isx of the padded
+// row are zero.  One thread per element.
 template <int KIND>
 __global__ void __launch_bounds__(256)
 pair_image_kernel(const __grid_constant__ PairBatch b, int isx, int isy, int pitch)
@@ -515,7 +524,7 @@ pair_image_kernel(const __grid_constant__ PairBatch b, int isx, int isy, int pit
     const float r = (c < isx) ? src[c] : 0.f;
     const size_t o = (size_t)k * pitch + c;
     if constexpr (KIND == kPairF32) {
-        reinterpret_cast<float2 *>(b.dst[i])[o] = make_float2(l, r);
+        reinterpret_cast<float2 *>(b.dst[i])[o] = make_float2(l, __fsub_rn(r, l));
     } else if constexpr (KIND == kPairF16) {
         const __half2 h = __floats2half2_rn(l, r);
         reinterpret_cast<__half2 *>(b.dst[i])[o] = h;

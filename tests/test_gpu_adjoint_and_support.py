@@ -183,3 +183,32 @@ def test_shared_memory_adjoint_matches_direct_and_oracle(L, scan):
     assert rel_l2(outs[1], outs[0]) <= 1e-6
     for o in outs:
         assert rel_l2(o, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["phantom", "zero_mean"])
+def test_adjoint_full_detector_512(kind):
+    """512^3 -> 4 projections of the full 1248x960 detector (the coordinate
+    range where float32 centring matters), against the oracle's adjoint:
+    the voxelised 50-ellipsoid phantom, and a zero-mean random volume (the
+    gradient-like input of the autograd backward)."""
+    scan = synth.SCANS["full"]
+    vol = synth.Volume(512)
+    A = oracle.carm_matrices(scan)[[0, 124, 248, 371]]
+    if kind == "phantom":
+        f = oracle.ellipsoid_voxelize(vol.L, vol.R, vol.O, synth.ellipsoids(50, seed=2, scan=scan)).astype(np.float32)
+    else:
+        f = (synth.uniform_volume(vol.L, seed=9) - 0.5).astype(np.float32)
+    ref = oracle.adjoint(vol.L, vol.R, vol.O, f.astype(np.float64), A, scan.isx, scan.isy)
+    with make_bp(vol, scan) as bp:
+        got = bp.adjoint(torch.from_numpy(f).cuda(), A).cpu().numpy()
+    err = rel_l2(got, ref)
+    # A pixel of B^T f sums thousands of voxel terms; with mixed signs the
+    # sum is far smaller than the sum of magnitudes, and float32 rounding of
+    # the terms and of the accumulation scales with the latter.  The error
+    # is therefore measured against B^T |f| (equal to B^T f for the
+    # nonnegative phantom).
+    scale = np.linalg.norm(oracle.adjoint(vol.L, vol.R, vol.O, np.abs(f).astype(np.float64), A, scan.isx,
+                                          scan.isy)) if kind == "zero_mean" else np.linalg.norm(ref)
+    err_abs = np.linalg.norm(got - ref) / scale
+    print(f"adjoint 512^3 -> 4 x 1248x960 {kind}: rel-L2 {err:.3e}, against B^T|f| {err_abs:.3e}")
+    assert err_abs <= 1e-5
