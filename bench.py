@@ -55,7 +55,7 @@ UNIT = "GUP/s"
 FP32_PER_SM_CLK = 128.0
 FP32_INSTR_PER_UPDATE = 20.5
 ISSUE_PER_SM_CLK = 128.0
-INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 34.1}
+INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 31.9}
 MUFU_PER_SM_CLK = 16.0
 SMEM_BYTES_PER_SM_CLK = 128.0
 TMA_SMEM_BYTES_PER_UPDATE = 16.0 + 114 * 32 * 8 / (32 * 16 * 8)

@@ -161,12 +161,13 @@ def test_gpu_matrices_match_oracle():
 
 
 @pytest.mark.parametrize("L,dtype,tol", [(512, "f32", FP32_TOL), (512, "f16", FP16_TOL), (512, "bf16", BF16_TOL),
-                                         (1024, "f16", FP16_TOL), (1024, "bf16", BF16_TOL)])
+                                         (1024, "f32", FP32_TOL), (1024, "f16", FP16_TOL),
+                                         (1024, "bf16", BF16_TOL)])
 def test_full_size_sampled_voxels(L, dtype, tol):
-    """512^3 (and the 1024^3 precision form) x 496 x 1248x960, uniform timing
-    stack, in the launch configuration the benchmark times (batches of 64,
-    device input, default path); the oracle evaluates 4096 sampled voxels one
-    by one."""
+    """512^3 and 1024^3 x 496 x 1248x960, uniform timing stack, in the launch
+    configuration the benchmark times (batches of 64, device input, default
+    path: TMA for f32, texture for 16-bit); the oracle evaluates 4096
+    sampled voxels one by one."""
     api = native()
     scan, vol = synth.SCANS["full"], synth.Volume(L)
     A = oracle.carm_matrices(scan)
