@@ -234,6 +234,21 @@ def cpu_baseline(L: int, n_sample: int):
                       f"{dt:.1f} s", "seconds": round(dt, 2)}
 
 
+def cpu_baseline_one_core(L: int, n_sample: int):
+    """The same oracle on one host core (OMP_NUM_THREADS=1, read when the
+    oracle library loads), in a child process started by fork+exec, so the
+    parent's CUDA context is not inherited."""
+    import subprocess
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_baseline(%d, %d)))" % (ROOT, L, n_sample))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": d["cores"], "sample": d["sample"]}
+
+
 def run_reference(args, rank: int):
     """Reference arm: the FP64 oracle (there is no reference implementation
     of the paper's code) on the host cores, each step a bounded sample of the
@@ -462,6 +477,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(args.L, args.cpu_proj)
+        cpu["one_core"] = cpu_baseline_one_core(args.L, max(1, args.cpu_proj // 16))
     line = {
         "metric": METRIC, "value": f32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": f32["ms_per_step"], "higher_is_better": True,
