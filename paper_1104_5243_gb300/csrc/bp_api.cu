@@ -88,6 +88,8 @@ struct bp_ctx {
     bool block_centre = true;      // BP_OPT_BLOCK_CENTRE (float32 projections)
     float4 *centres[2] = {nullptr, nullptr};
     long long centre_blocks[2] = {0, 0};
+    int4 *boxes[2] = {nullptr, nullptr};   // TMA path: per-(brick, projection) box decisions
+    long long box_bricks[2] = {0, 0};
     size_t ev_used = 0;
     char err[1024] = "no error";
 };
@@ -150,6 +152,8 @@ static void release(bp_ctx *c)
             cudaFree(c->masks[s]);
         if (c->centres[s])
             cudaFree(c->centres[s]);
+        if (c->boxes[s])
+            cudaFree(c->boxes[s]);
     }
     if (c->work_dev)
         cudaFree(c->work_dev);
@@ -571,8 +575,25 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 centres = c->centres[s];
                 centre_batch(&cb, &rows[0][0][0], m, c->O, c->R);
             }
+            int4 *boxes = nullptr;
+            BoxSpec bs{};
+            if (tma) {
+                if (nb > c->box_bricks[s]) {
+                    if (c->boxes[s])
+                        CTX_CK(c, cudaFree(c->boxes[s]));
+                    c->boxes[s] = nullptr;
+                    c->box_bricks[s] = 0;
+                    CTX_CK(c, cudaMalloc((void **)&c->boxes[s], sizeof(int4) * kMaxBatch * nb));
+                    c->box_bricks[s] = nb;
+                }
+                boxes = c->boxes[s];
+                const int kind = pair_kind(c);
+                bs = kind == kPairF32 ? BoxSpec{TmaBox<kPairF32>::BU, TmaBox<kPairF32>::BV, kPairAlign<kPairF32>}
+                                      : BoxSpec{TmaBox<kPairF16>::BU, TmaBox<kPairF16>::BV, kPairAlign<kPairF16>};
+            }
             CTX_CK(c, launch_block_prepass(b, centres ? &cb : nullptr, g, c->isx, c->isy, tile[0], tile[1], tile[2],
-                                           masks, centres, masks ? c->work_dev : nullptr, c->copy_stream));
+                                           masks, centres, boxes ? &bs : nullptr, boxes,
+                                           masks ? c->work_dev : nullptr, c->copy_stream));
         }
         CTX_CK(c, cudaEventRecord(c->copy_done[s], c->copy_stream));
         CTX_CK(c, cudaStreamWaitEvent(c->stream, c->copy_done[s], 0));
@@ -598,6 +619,7 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 tb.img[j] = static_cast<const char *>(c->pairs[s]) + c->pair_slot_bytes * j;
             }
             tb.centres = centres;
+            tb.boxes = c->boxes[s];
             tb.bricks = nb;
             CTX_CK(c, launch_bp_tma(tb, c->vol, g, pair_kind(c), !c->vol_zero, c->ieee_rcp, c->err_dev, c->work_dev,
                                     c->stream));

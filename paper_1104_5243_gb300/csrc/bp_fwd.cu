@@ -333,9 +333,51 @@ __device__ BlockRec block_centre(const FwdBatch &b, const CentreBatch &cb, int i
     return rec;
 }
 
-// One thread per block of the texture kernel, looping over the projections
-// of the batch (a warp-uniform index: the matrices are read from kernel
-// parameter space by broadcast).  Records are stored as three planes
+// TMA-path box decision of one (brick, projection): the pair columns and
+// image rows the brick's corner projections touch, with a pixel of margin
+// (pair column = floor(u') + ku; top row = floor(v') + kv - 1), decide
+// between culling, one staged box, and the global-memory path.  kb are the
+// offsets the kernel's floor(u'), floor(v') are relative to.
+__device__ int4 tma_box(const FwdBatch &b, int i, const VolGeom &g, int isx, int isy, int x0, int y0, int z0,
+                        int x1, int y1, int z1, int2 kb, const BoxSpec &bs)
+{
+    const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float X = fmaf(g.R, (float)((c & 1) ? x1 : x0), g.Ox);
+        const float Y = fmaf(g.R, (float)((c & 2) ? y1 : y0), g.Oy);
+        const float Z = fmaf(g.R, (float)((c & 4) ? z1 : z0), g.Oz);
+        const float w = fmaf(rw.x, X, fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w)));
+        const float r = 1.0f / w;
+        const float u = fmaf(ru.x, X, fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w))) * r;
+        const float v = fmaf(rv.x, X, fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w))) * r;
+        umin = fminf(umin, u);
+        umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v);
+        vmax = fmaxf(vmax, v);
+    }
+    // keep the int conversions in range
+    umin = fminf(fmaxf(umin, -1.0e6f), 1.0e6f);
+    umax = fminf(fmaxf(umax, -1.0e6f), 1.0e6f);
+    vmin = fminf(fmaxf(vmin, -1.0e6f), 1.0e6f);
+    vmax = fminf(fmaxf(vmax, -1.0e6f), 1.0e6f);
+    const int ku = (int)b.k[i].x, kv = (int)b.k[i].y;
+    const int cmin = (int)floorf(umin) + ku - 1, cmax = (int)floorf(umax) + ku + 1;
+    const int rmin = (int)floorf(vmin) + kv - 2, rmax = (int)floorf(vmax) + kv + 1;
+    if (cmax < 0 || cmin > isx || rmax < 0 || rmin > isy - 1)
+        return make_int4(0, 0, 0, 0);   // nothing of this brick lands on the detector
+    const int cx0 = cmin & ~(bs.align - 1), ry0 = rmin;
+    if (cmax < cx0 + bs.bu && rmax < ry0 + bs.bv) {
+        const int cu = kb.x - cx0, cv = kb.y - 1 - ry0;
+        return make_int4(1, __float_as_int((float)(cv * bs.bu + cu) + 12582912.0f), cx0, ry0);
+    }
+    return make_int4(2, kb.x, kb.y - 1, 0);
+}
+
+// One thread per tile (the texture kernel's block or the TMA path's brick),
+// looping over the projections of the batch (a warp-uniform index: the
+// matrices are read from kernel parameter space by broadcast).  Records are stored as three planes
 // (u, v, w parts), projection-major within each, centres[(part * 64 + i) *
 // nblocks + block], so a warp's stores are contiguous.  The kept
 // updates are summed per warp into the context's work counter (for the
@@ -344,8 +386,8 @@ template <bool CENTRES>
 __global__ void __launch_bounds__(256)
 block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__ CentreBatch cb, const VolGeom g,
                      int isx, int isy, int tx, int ty, int tz, int nbx, int nby, long long nblocks,
-                     unsigned long long *__restrict__ masks, float4 *__restrict__ centres,
-                     unsigned long long *__restrict__ work)
+                     unsigned long long *__restrict__ masks, float4 *__restrict__ centres, const BoxSpec bs,
+                     int4 *__restrict__ boxes, unsigned long long *__restrict__ work)
 {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long done = 0;
@@ -357,12 +399,16 @@ block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__
         for (int i = 0; i < b.n; ++i) {
             if (masks && footprint_hits(b, i, g, isx, isy, x0, y0, z0, x1, y1, z1))
                 m |= 1ull << i;
+            int2 kb = make_int2((int)b.k[i].x, (int)b.k[i].y);
             if constexpr (CENTRES) {
                 const BlockRec rec = block_centre(b, cb, i, x0 + x1, y0 + y1, z0 + z1);
                 centres[((size_t)0 * kMaxBatch + i) * nblocks + q] = rec.u;
                 centres[((size_t)1 * kMaxBatch + i) * nblocks + q] = rec.v;
                 centres[((size_t)2 * kMaxBatch + i) * nblocks + q] = rec.w;
+                kb = make_int2((int)rec.w.y, (int)rec.w.z);
             }
+            if (boxes)
+                boxes[(size_t)i * nblocks + q] = tma_box(b, i, g, isx, isy, x0, y0, z0, x1, y1, z1, kb, bs);
         }
         if (masks) {
             masks[q] = m;
@@ -377,20 +423,23 @@ block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__
 
 cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const VolGeom &g, int isx, int isy,
                                  int tx, int ty, int tz, unsigned long long *masks, float4 *centres,
-                                 unsigned long long *work, cudaStream_t s)
+                                 const BoxSpec *box, int4 *boxes, unsigned long long *work, cudaStream_t s)
 {
-    if (b.n <= 0 || (!masks && !centres))
+    if (b.n <= 0 || (!masks && !centres && !boxes))
         return cudaSuccess;
+    const BoxSpec bs = box ? *box : BoxSpec{1, 1, 1};
+    if (!box)
+        boxes = nullptr;
     const int nbx = (g.L + tx - 1) / tx, nby = (g.L + ty - 1) / ty;
     const long long nblocks = tile_count(g.L, tx, ty, tz);
     const unsigned grid = (unsigned)((nblocks + 255) / 256);
     if (centres && cb) {
         block_prepass_kernel<true><<<grid, 256, 0, s>>>(b, *cb, g, isx, isy, tx, ty, tz, nbx, nby, nblocks, masks,
-                                                        centres, work);
+                                                        centres, bs, boxes, work);
     } else {
         static const CentreBatch none = {};
         block_prepass_kernel<false><<<grid, 256, 0, s>>>(b, none, g, isx, isy, tx, ty, tz, nbx, nby, nblocks, masks,
-                                                         nullptr, work);
+                                                         nullptr, bs, boxes, work);
     }
     return cudaGetLastError();
 }

@@ -101,9 +101,23 @@ cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int t
 void fwd_tile(int lanes_x, int *tx, int *ty, int *tz);
 long long fwd_blocks(int L, int lanes_x);
 long long tile_count(int L, int tx, int ty, int tz);
+// TMA-path box decision per (brick, projection), made by the pre-pass
+// (boxes, one int4 per pair at index projection * bricks + brick):
+//   (0, 0, 0, 0)            the footprint misses the detector: skip;
+//   (1, off, cx0, ry0)      load the BU x BV pair box at pair column cx0,
+//                           row ry0; off = float bits of (row offset * BU +
+//                           column offset + 1.5 * 2^23), see bp_tma.cu;
+//   (2, cu, cv, 0)          footprint larger than the box: read the pair
+//                           image from global memory, pair column floor(u')
+//                           + cu, top row floor(v') + cv.
+// The offsets are relative to the brick's centring offsets with per-brick
+// centring, else to the projection's.
+struct BoxSpec {
+    int bu, bv, align;   // box columns and rows (pairs), column alignment (pairs)
+};
 cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const VolGeom &g, int isx, int isy,
                                  int tx, int ty, int tz, unsigned long long *masks, float4 *centres,
-                                 unsigned long long *work, cudaStream_t s);
+                                 const BoxSpec *box, int4 *boxes, unsigned long long *work, cudaStream_t s);
 
 // smem: accumulate each block's footprint in shared memory (kAdjTile pixels
 // at most) and add it to the image with one atomic per touched pixel.
@@ -143,6 +157,7 @@ struct TmaBatch {
     int2 k[kMaxBatch];                 // integer centring offsets (ku, kv)
     const void *img[kMaxBatch];        // pair image base, for the global path
     const float4 *centres;             // per-brick centring records (NULL: per projection)
+    const int4 *boxes;                 // per-(brick, projection) box decisions (pre-pass)
     long long bricks;                  // bricks of the volume (record plane stride)
     int n, isx, isy, pitch;            // pitch: pair elements per row
 };

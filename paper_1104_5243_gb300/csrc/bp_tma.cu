@@ -4,17 +4,21 @@
 //
 // Why: the texture unit returns 2x2 gathers of 32-bit texels at half the
 // rate of 16-bit ones, which bounds the float32 form of the texture kernel.
-// Here each block owns a 32 x 16 x 8 voxel brick; for every projection a
-// producer warp projects the brick's 8 corners (one lane each), and either
-//   * culls the projection when the footprint misses the detector (every
+// Here each block owns a 32 x 16 x 8 voxel brick.  For every projection the
+// per-tile pre-pass (bp_fwd.cu) has projected the brick's 8 corners and
+// decided to
+//   * cull the projection when the footprint misses the detector (every
 //     term is then exactly zero -- the line-wise clipping of Sect. 3.3 at
 //     brick granularity), or
-//   * issues one cp.async.bulk.tensor.2d load of the footprint box from the
-//     projection's "pair image" into a stage of a shared-memory ring,
+//   * load the footprint box of the projection's "pair image" with one
+//     cp.async.bulk.tensor.2d into a stage of a shared-memory ring,
 //     completing on an mbarrier; out-of-range rows/columns are zero-filled
 //     by the TMA unit, which is the zero padding of Sect. 3.3, or
-//   * (footprint larger than the box) marks the projection for the
-//     bounds-checked global-memory path.
+//   * (footprint larger than the box) use the bounds-checked global-memory
+//     path.
+// The block stages those decisions; one producer lane issues the copies of
+// the projections the brick computes, and the consumers skip culled ones
+// without touching the ring.
 // The pair image stores element c = (p[c-1], p[c]) of each row (zero outside
 // the detector), so the four corners of an update are two shared-memory
 // loads: (tl, tr) from row iv and (bl, br) from row iv+1.  Float32 pairs
@@ -178,11 +182,13 @@ __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const floa
     using P = Pairs<KIND>;
     using T = typename P::T;
     constexpr int BU = TmaBox<KIND>::BU;
-    // SMEM: mt.y holds the bits of off = (row offset) * BU + (column offset)
-    // + 1.5 * 2^23, so fv0 * BU + fu0 + off is the element index of the top
-    // pair in the staged box, plus the magic, exactly (all integers far below
-    // 2^22); its bits times the pair size, plus (tile - magic bits * pair
-    // size) modulo 2^32, are the shared address.
+    // mt is the box decision (1, off, cx0, ry0) or (2, cu, cv, 0).  SMEM:
+    // off holds the bits of (row offset) * BU + (column offset) + 1.5 * 2^23,
+    // so fv0 * BU + fu0 + off is the element index of the top pair in the
+    // staged box, plus the magic, exactly (all integers far below 2^22); its
+    // bits times the pair size, plus (tile - magic bits * pair size) modulo
+    // 2^32, are the shared address.  Global: pair column floor(u') + cu, top
+    // row floor(v') + cv.
     const float off = __int_as_float(mt.y);
     const uint32_t base = tile - kIntMagicBits * (uint32_t)sizeof(T);
 #pragma unroll
@@ -210,8 +216,8 @@ __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const floa
                 bot = P::template load<BU * (int)sizeof(T)>(a);
             } else {
                 // rows outside the detector are zero
-                const int col = int_of_integral(fu0) + mt.z;
-                const int row = int_of_integral(fv0) + mt.w;
+                const int col = int_of_integral(fu0) + mt.y;
+                const int row = int_of_integral(fv0) + mt.z;
                 const T *img = reinterpret_cast<const T *>(b.img[i]);
                 const bool cok = col >= 0 && col <= b.isx;
                 const T *p = img + (long long)row * b.pitch + col;
@@ -253,13 +259,11 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     extern __shared__ __align__(128) unsigned char dyn_smem[];   // the ring: S stages of kBufElems pairs
     T (*buf)[kBufElems] = reinterpret_cast<T (*)[kBufElems]>(dyn_smem);
     __shared__ __align__(8) uint64_t full[S], empty[S];
-    // per stage: mode (0 culled, 1 shared memory, 2 global), the element
-    // offset of the staged box as float bits (mode 1), and the column / row
-    // offsets that turn floor(u'), floor(v') into indices of the global pair
-    // image (mode 2)
-    __shared__ int4 meta[S];
-    // BLK: the brick's centring records of every projection of the batch
-    // (u row, v row, (w_c, ku_b, kv_b)), staged once
+    // the brick's box decision for every projection of the batch (made by
+    // the pre-pass: culled / staged box / global path, with its offsets),
+    // and with BLK its centring records (u row, v row, (w_c, ku_b, kv_b)),
+    // staged once
+    __shared__ int4 box[kMaxBatch];
     __shared__ float4 rec[3][BLK ? kMaxBatch : 1];
     __shared__ int abort_flag;
 
@@ -276,6 +280,8 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
+    if (threadIdx.x < kMaxBatch && threadIdx.x < b.n)
+        box[threadIdx.x] = b.boxes[(size_t)threadIdx.x * b.bricks + brick];
     if constexpr (BLK) {
         if (threadIdx.x < 3 * kMaxBatch) {
             const int part = threadIdx.x / kMaxBatch, i = threadIdx.x % kMaxBatch;
@@ -286,85 +292,43 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     __syncthreads();
 
     if (warp == kConsumerWarps) {
-        // ---------------- producer: classify each projection, start copies
-        const int xe = min(bx0 + kBrickX, L) - 1, ye = min(by0 + kBrickY, L) - 1, ze = min(bz0 + kBrickZ, L) - 1;
-        const int c = lane & 7;   // lanes 0..7 take one brick corner each
-        const float X = fmaf(g.R, (float)((c & 1) ? xe : bx0), g.Ox);
-        const float Yc = fmaf(g.R, (float)((c & 2) ? ye : by0), g.Oy);
-        const float Z = fmaf(g.R, (float)((c & 4) ? ze : bz0), g.Oz);
+        // ---------------- producer: one lane starts the copies of the
+        // projections the brick computes, in order, into the ring
+        if (lane != 0)
+            return;
         int issued = 0;            // stages whose tile may still be in flight
-        unsigned long long computed = 0;   // projections this brick computes
         int last_use[S] = {};      // use index of each stage's last tile
+        unsigned long long computed = 0;
+        int k = 0;                 // projections computed so far
         for (int i = 0; i < b.n; ++i) {
-            const int st = i % S, use = i / S;
+            const int4 bi = box[i];
+            if (bi.x == 0)
+                continue;          // culled: no stage, no barrier
+            const int st = k % S, use = k / S;
+            ++k;
             if (use > 0 && !mbar_wait_bounded(&empty[st], (use - 1) & 1)) {
-                if (lane == 0) {
-                    atomicExch(&abort_flag, 1);
-                    atomicExch(err, 1);
-                }
+                atomicExch(&abort_flag, 1);
+                atomicExch(err, 1);
                 break;
             }
             if (*(volatile int *)&abort_flag)
                 break;
-            const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
-            const float w = fmaf(rw.x, X, fmaf(rw.y, Yc, fmaf(rw.z, Z, rw.w)));
-            // the box has a pixel of margin: the approximate reciprocal (about
-            // 1 ulp) is far more accurate than the corners need
-            const float r = recip_tma<false>(w);
-            const float u = fmaf(ru.x, X, fmaf(ru.y, Yc, fmaf(ru.z, Z, ru.w))) * r;
-            const float v = fmaf(rv.x, X, fmaf(rv.y, Yc, fmaf(rv.z, Z, rv.w))) * r;
-            float umin = u, umax = u, vmin = v, vmax = v;
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-                umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
-                umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-                vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-                vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            ++computed;
+            if (bi.x == 1) {
+                mbar_expect_tx(&full[st], (uint32_t)(kBufElems * sizeof(T)));
+                tma_load_2d(buf[st], &b.map[i], bi.z * kPairWords<KIND>, bi.w, &full[st]);
+                issued |= 1 << st;
+                last_use[st] = use;
+            } else {
+                mbar_arrive(&full[st]);
+                issued &= ~(1 << st);
             }
-            if (lane == 0) {
-                const int2 kc = b.k[i];
-                // offsets the consumers' floor(u'), floor(v') are relative to:
-                // the projection's, or with BLK the brick's (the box itself
-                // does not depend on the centring)
-                int2 kb = kc;
-                if constexpr (BLK)
-                    kb = make_int2((int)rec[2][i].y, (int)rec[2][i].z);
-                umin = fminf(fmaxf(umin, -1.0e6f), 1.0e6f);   // keep the int conversions in range
-                umax = fminf(fmaxf(umax, -1.0e6f), 1.0e6f);
-                vmin = fminf(fmaxf(vmin, -1.0e6f), 1.0e6f);
-                vmax = fminf(fmaxf(vmax, -1.0e6f), 1.0e6f);
-                // pair columns and image rows touched, one pixel of margin
-                // (pair column = floor(u') + ku; top row = floor(v') + kv - 1)
-                const int cmin = (int)floorf(umin) + kc.x - 1, cmax = (int)floorf(umax) + kc.x + 1;
-                const int rmin = (int)floorf(vmin) + kc.y - 2, rmax = (int)floorf(vmax) + kc.y + 1;
-                int mode, cx0 = 0, ry0 = 0;
-                if (cmax < 0 || cmin > b.isx || rmax < 0 || rmin > b.isy - 1) {
-                    mode = 0;   // nothing of this brick lands on the detector
-                } else {
-                    cx0 = cmin & ~(kPairAlign<KIND> - 1);
-                    ry0 = rmin;
-                    mode = (cmax < cx0 + BU && rmax < ry0 + BV) ? 1 : 2;
-                    if (mode == 2)
-                        cx0 = ry0 = 0;   // the global path indexes the whole pair image
-                }
-                const int cu = kb.x - cx0, cv = kb.y - 1 - ry0;
-                meta[st] = make_int4(mode, __float_as_int((float)(cv * BU + cu) + kIntMagic), cu, cv);
-                computed += mode != 0;
-                if (mode == 1) {
-                    mbar_expect_tx(&full[st], (uint32_t)(kBufElems * sizeof(T)));   // also publishes meta
-                    tma_load_2d(buf[st], &b.map[i], cx0 * kPairWords<KIND>, ry0, &full[st]);
-                    issued |= 1 << st;
-                    last_use[st] = use;
-                } else {
-                    mbar_arrive(&full[st]);
-                    issued &= ~(1 << st);
-                }
-            }
-            __syncwarp();
         }
-        if (lane == 0 && computed)
+        if (computed) {
+            const int xe = min(bx0 + kBrickX, L) - 1, ye = min(by0 + kBrickY, L) - 1, ze = min(bz0 + kBrickZ, L) - 1;
             atomicAdd(work, computed * (unsigned long long)((xe - bx0 + 1) * (ye - by0 + 1) * (ze - bz0 + 1)));
-        if (lane == 0 && *(volatile int *)&abort_flag) {
+        }
+        if (*(volatile int *)&abort_flag) {
             // let copies still in flight land before the block's memory goes away
             for (int q = 0; q < S; ++q)
                 if (issued & (1 << q))
@@ -407,6 +371,9 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     uint32_t phase = 0;
 #pragma unroll 1
     for (int i = 0; i < b.n; ++i) {
+        const int4 mt = box[i];
+        if (mt.x == 0)
+            continue;   // culled by the pre-pass: every term is exactly zero
         if (!mbar_wait_bounded(&full[s], phase)) {
             if (lane == 0) {
                 atomicExch(&abort_flag, 1);
@@ -415,8 +382,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
             ok = false;
             break;
         }
-        const int4 mt = meta[s];
-        if (mt.x != 0) {
+        {
             float4 ru, rv, rw = b.m[i][2];
             if constexpr (BLK) {
                 ru = rec[0][i];
