@@ -49,16 +49,16 @@ UNIT = "GUP/s"
 #   gather: the texture unit's 2x2-gather rate for the storage type, MEASURED
 #     on this GPU by bp_probe_gather (one gather per update).
 # TMA kernel (bp_tma_kernel):
-#   smem: 128 B per SM per clock of shared-memory bandwidth over 23.1 B per
-#     update: two 8-byte pair loads, plus the TMA fill of the 114 x 32-pair box
-#     (29184 B) per 32 x 16 x 8-voxel brick and projection.
+#   smem: 128 B per SM per clock of shared-memory bandwidth over 24.0 B per
+#     update: two 8-byte pair loads, plus the TMA fill of the 114 x 36-pair box
+#     (32832 B) per 32 x 16 x 8-voxel brick and projection.
 FP32_PER_SM_CLK = 128.0
 FP32_INSTR_PER_UPDATE = 20.5
 ISSUE_PER_SM_CLK = 128.0
-INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 31.9}
+INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 28.7}
 MUFU_PER_SM_CLK = 16.0
 SMEM_BYTES_PER_SM_CLK = 128.0
-TMA_SMEM_BYTES_PER_UPDATE = 16.0 + 114 * 32 * 8 / (32 * 16 * 8)
+TMA_SMEM_BYTES_PER_UPDATE = 16.0 + 114 * 36 * 8 / (32 * 16 * 8)
 
 
 def roofline_peak_gups(path: str, form: str, sm_mhz: float, sms: int, gather_per_sm_clk: float) -> dict:

@@ -131,18 +131,19 @@ cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom
 // projections staged as "pair images" (element c of a row holds pixels c-1
 // and c; for float32, pixel c-1 and the difference of c and c-1) and loaded
 // per brick and projection as one TMA box of BU pair
-// columns by BV rows.  A box of that size holds the footprint of 97 % of the
-// visible (brick, projection) pairs of the 512^3 C-arm scan; larger
-// footprints (bricks near the source) read the pair image from global memory.
+// columns by BV rows.  A box of that size holds the footprint of 99.9 % of
+// the visible (brick, projection) pairs of the 512^3 C-arm scan (97 % with
+// 32 rows); larger footprints (bricks near the source) read the pair image
+// from global memory.
 constexpr int kBrickX = 32, kBrickY = 16, kBrickZ = 8;
 enum PairKind { kPairF32 = 0, kPairF16 = 1, kPairBF16 = 2 };
 template <int KIND> struct TmaBox;
 // Row pitches of 228 words (f32 pairs) and 100 words (16-bit pairs), both
 // 4 modulo 32, put successive box rows 4 banks apart, so lanes on the same
 // column in different rows do not conflict.
-template <> struct TmaBox<kPairF32> { static constexpr int BU = 114, BV = 32, S = 2; };
-template <> struct TmaBox<kPairF16> { static constexpr int BU = 100, BV = 32, S = 3; };
-template <> struct TmaBox<kPairBF16> { static constexpr int BU = 100, BV = 32, S = 3; };
+template <> struct TmaBox<kPairF32> { static constexpr int BU = 114, BV = 36, S = 2; };
+template <> struct TmaBox<kPairF16> { static constexpr int BU = 100, BV = 36, S = 3; };
+template <> struct TmaBox<kPairBF16> { static constexpr int BU = 100, BV = 36, S = 3; };
 // 32-bit words per pair, and the pair-column alignment that keeps the TMA
 // box origin on a 16-byte boundary.
 template <int KIND> constexpr int kPairWords = KIND == kPairF32 ? 2 : 1;

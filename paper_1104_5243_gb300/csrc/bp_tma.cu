@@ -168,6 +168,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Shared-memory stride of a ring stage: the box rounded up to a multiple of
+// 128 bytes, the alignment a tensor copy's shared-memory destination needs.
+template <int KIND>
+struct TmaStage {
+    static constexpr int kBytes = (int)sizeof(typename Pairs<KIND>::T) * TmaBox<KIND>::BU * TmaBox<KIND>::BV;
+    static constexpr int kElems = ((kBytes + 127) / 128 * 128) / (int)sizeof(typename Pairs<KIND>::T);
+    static_assert(kElems * (int)sizeof(typename Pairs<KIND>::T) % 128 == 0, "stage stride must be 128-byte aligned");
+};
+
 // The 16 updates of one consumer lane for projection i (matrix rows ru, rv,
 // rw), reading the corner pairs from the staged tile (SMEM) or from the
 // global pair image; the two forms are separate loop bodies so neither
@@ -253,11 +262,12 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     using P = Pairs<KIND>;
     using T = typename P::T;
     constexpr int BU = TmaBox<KIND>::BU, BV = TmaBox<KIND>::BV;
-    constexpr int kBufElems = BU * BV;
+    constexpr int kBufElems = BU * BV;                  // pairs one box copy writes
+    constexpr int kStageElems = TmaStage<KIND>::kElems;   // stage stride: 128-byte multiple
     constexpr int S = TmaBox<KIND>::S;
     constexpr int kConsumerWarps = kThreads / 32;
-    extern __shared__ __align__(128) unsigned char dyn_smem[];   // the ring: S stages of kBufElems pairs
-    T (*buf)[kBufElems] = reinterpret_cast<T (*)[kBufElems]>(dyn_smem);
+    extern __shared__ __align__(128) unsigned char dyn_smem[];   // the ring: S stages of kStageElems pairs
+    T (*buf)[kStageElems] = reinterpret_cast<T (*)[kStageElems]>(dyn_smem);
     __shared__ __align__(8) uint64_t full[S], empty[S];
     // the brick's box decision for every projection of the batch (made by
     // the pre-pass: culled / staged box / global path, with its offsets),
@@ -429,7 +439,7 @@ static cudaError_t launch_tma_blk(const TmaBatch &b, float *vol, const VolGeom &
 {
     dim3 grid((g.L + kBrickX - 1) / kBrickX, (g.L + kBrickY - 1) / kBrickY, (g.L + kBrickZ - 1) / kBrickZ);
     using T = typename Pairs<KIND>::T;
-    const size_t smem = sizeof(T) * TmaBox<KIND>::BU * TmaBox<KIND>::BV * TmaBox<KIND>::S;
+    const size_t smem = sizeof(T) * TmaStage<KIND>::kElems * TmaBox<KIND>::S;
     // the ring exceeds the 48 KB default for float32 pairs (set per call:
     // cheap, and correct on whichever device is current)
     cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<KIND, IEEE, BLK>,
