@@ -120,7 +120,9 @@ bp_adjoint_kernel(const __grid_constant__ AdjBatch b, const float *__restrict__ 
 // of the block's box (w is affine).  A pixel's terms therefore sum in
 // magnitude to at most B = (sum of |f| over the block) * (max r^2 over the
 // box).  With B mapped to 2^30 no partial sum can overflow; a term is
-// rounded to 2^-31 B (float32 rounds to 2^-24 of the term itself).
+// rounded to 2^-31 B (float32 rounds to 2^-24 of the term itself): about
+// 1e-6 relative error on coarse detectors, below float32 order effects on
+// fine ones.
 // Same coordinates and weights as bp_adjoint_kernel.
 using AdjAcc = int;
 constexpr int kAccBits = 8 * (int)sizeof(AdjAcc);
@@ -131,12 +133,19 @@ __device__ __forceinline__ void red_shared_add(float *p, float v)
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
 }
 
+// Blocks of 32 x 32 x 4 voxels: each lane takes 4 voxels along x (8 apart)
+// and kAdjVPY along y (one per warp row, kWarpsY apart).  A block's
+// footprint grows with its x and y extent in u but its update count with
+// x * y, so the per-projection work of a block (plan, zeroing and flushing
+// its tile, barriers) is spread over 4096 updates.
+constexpr int kAdjVPY = 4;
+
 template <bool IEEE>
 __global__ void __launch_bounds__(kThreads)
 bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restrict__ vol, const VolGeom g,
                        float *__restrict__ out, int isx, int isy)
 {
-    constexpr int LX = 8, LZ = 32 / LX, TX = LX * kVoxPerLane;
+    constexpr int LX = 8, LZ = 32 / LX, TX = LX * kVoxPerLane, TY = kWarpsY * kAdjVPY;
     __shared__ __align__(16) AdjAcc tile[kAdjTile];
     // (x0, y0, W, H); W = 0 culled, W < 0 too large.  Two slots: warp 0
     // writes the next projection's plan while slower warps may still read
@@ -147,27 +156,35 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
     const int lane = threadIdx.x & 31;
     const int tx = lane % LX, tz = lane / LX;
     const int L = g.L;
-    const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * kWarpsY, bz0 = blockIdx.z * LZ;
+    const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY, bz0 = blockIdx.z * LZ;
     const int xb = bx0 + tx;
-    const int y = by0 + (threadIdx.x >> 5);
+    const int yb = by0 + (threadIdx.x >> 5);   // this lane's rows: yb + kWarpsY * ky
     const int z = bz0 + tz;
-    const bool live = y < L && z < L;
 
-    float f[kVoxPerLane], X[kVoxPerLane];
+    float f[kAdjVPY][kVoxPerLane], X[kVoxPerLane], Y[kAdjVPY];
 #pragma unroll
-    for (int k = 0; k < kVoxPerLane; ++k) {
-        const int x = xb + LX * k;
-        f[k] = (live && x < L) ? vol[((size_t)z * L + y) * L + x] : 0.f;
-        X[k] = fmaf(g.R, (float)x, g.Ox);
+    for (int k = 0; k < kVoxPerLane; ++k)
+        X[k] = fmaf(g.R, (float)(xb + LX * k), g.Ox);
+#pragma unroll
+    for (int ky = 0; ky < kAdjVPY; ++ky) {
+        const int y = yb + kWarpsY * ky;
+        const bool live = y < L && z < L;
+        Y[ky] = fmaf(g.R, (float)y, g.Oy);
+#pragma unroll
+        for (int k = 0; k < kVoxPerLane; ++k) {
+            const int x = xb + LX * k;
+            f[ky][k] = (live && x < L) ? vol[((size_t)z * L + y) * L + x] : 0.f;
+        }
     }
-    const float Y = fmaf(g.R, (float)y, g.Oy);
     const float Z = fmaf(g.R, (float)z, g.Oz);
     // sum of |f| over the block, for the fixed-point scale (rounded up by
     // the factor applied to B below)
     float fm = 0.f;
 #pragma unroll
-    for (int k = 0; k < kVoxPerLane; ++k)
-        fm += fabsf(f[k]);
+    for (int ky = 0; ky < kAdjVPY; ++ky)
+#pragma unroll
+        for (int k = 0; k < kVoxPerLane; ++k)
+            fm += fabsf(f[ky][k]);
     for (int o = 16; o > 0; o >>= 1)
         fm += __shfl_xor_sync(0xffffffffu, fm, o);
     if (lane == 0)
@@ -178,7 +195,7 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
     for (int w8 = 0; w8 < kThreads / 32; ++w8)
         fsum_blk += fsum_warp[w8];
     // corner of the block's voxel box taken by lane c < 8 of warp 0
-    const int xe = min(bx0 + TX, L) - 1, ye = min(by0 + kWarpsY, L) - 1, ze = min(bz0 + LZ, L) - 1;
+    const int xe = min(bx0 + TX, L) - 1, ye = min(by0 + TY, L) - 1, ze = min(bz0 + LZ, L) - 1;
     const float CX = fmaf(g.R, (float)((lane & 1) ? xe : bx0), g.Ox);
     const float CY = fmaf(g.R, (float)((lane & 2) ? ye : by0), g.Oy);
     const float CZ = fmaf(g.R, (float)((lane & 4) ? ze : bz0), g.Oz);
@@ -247,59 +264,62 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
         }
         const float ulo = (float)(-1 - kc.x), uhi = (float)(isx - kc.x);
         const float vlo = (float)(-1 - kc.y), vhi = (float)(isy - kc.y);
-        const float bu = fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w));
-        const float bv = fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w));
-        const float bw = fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w));
 #pragma unroll
-        for (int k = 0; k < kVoxPerLane; ++k) {
-            if (f[k] == 0.f)
-                continue;
-            const float uw = fmaf(ru.x, X[k], bu);
-            const float vw = fmaf(rv.x, X[k], bv);
-            const float w = fmaf(rw.x, X[k], bw);
-            const float r = recip_adj<IEEE>(w);
-            const float u = uw * r, v = vw * r;
-            if (!(u > ulo && u < uhi && v > vlo && v < vhi))
-                continue;
-            const float fu0 = floorf(u), fv0 = floorf(v);
-            const int iu = (int)fu0 + kc.x, iv = (int)fv0 + kc.y;
-            const float fu = u - fu0, fv = v - fv0;
-            const float s = f[k] * (r * r);
-            const float sb = s * fv, st = s - sb;
-            const float w_tr = st * fu, w_tl = st - w_tr;
-            const float w_br = sb * fu, w_bl = sb - w_br;
-            const bool in_l = iu >= 0, in_r = iu + 1 < isx, in_t = iv >= 0, in_b = iv + 1 < isy;
-            if (tiled) {
-                // index in the tile; the footprint box covers every in-detector
-                // corner, the unsigned clamp only guards the array
-                const int q0 = (iv - p.y) * p.z + (iu - p.x);
-                auto at = [&](int d) { return &tile[min((unsigned)(q0 + d), (unsigned)(kAdjTile - 1))]; };
-                auto add = [&](int d, float t) {
-                    if constexpr (kAccFloat)
-                        red_shared_add(at(d), t);
-                    else if constexpr (sizeof(AdjAcc) == 8)   // two's complement add
-                        atomicAdd(reinterpret_cast<unsigned long long *>(at(d)),
-                                  (unsigned long long)__float2ll_rn(t * sc.x));
-                    else
-                        atomicAdd(at(d), __float2int_rn(t * sc.x));
-                };
-                if (in_t) {
-                    if (in_l) add(0, w_tl);
-                    if (in_r) add(1, w_tr);
-                }
-                if (in_b) {
-                    if (in_l) add(p.z, w_bl);
-                    if (in_r) add(p.z + 1, w_br);
-                }
-            } else {
-                const long long base = (long long)iv * isx + iu;
-                if (in_t) {
-                    if (in_l) atomicAdd(img + base, w_tl);
-                    if (in_r) atomicAdd(img + base + 1, w_tr);
-                }
-                if (in_b) {
-                    if (in_l) atomicAdd(img + base + isx, w_bl);
-                    if (in_r) atomicAdd(img + base + isx + 1, w_br);
+        for (int ky = 0; ky < kAdjVPY; ++ky) {
+            const float bu = fmaf(ru.y, Y[ky], fmaf(ru.z, Z, ru.w));
+            const float bv = fmaf(rv.y, Y[ky], fmaf(rv.z, Z, rv.w));
+            const float bw = fmaf(rw.y, Y[ky], fmaf(rw.z, Z, rw.w));
+#pragma unroll
+            for (int k = 0; k < kVoxPerLane; ++k) {
+                if (f[ky][k] == 0.f)
+                    continue;
+                const float uw = fmaf(ru.x, X[k], bu);
+                const float vw = fmaf(rv.x, X[k], bv);
+                const float w = fmaf(rw.x, X[k], bw);
+                const float r = recip_adj<IEEE>(w);
+                const float u = uw * r, v = vw * r;
+                if (!(u > ulo && u < uhi && v > vlo && v < vhi))
+                    continue;
+                const float fu0 = floorf(u), fv0 = floorf(v);
+                const int iu = (int)fu0 + kc.x, iv = (int)fv0 + kc.y;
+                const float fu = u - fu0, fv = v - fv0;
+                const float s = f[ky][k] * (r * r);
+                const float sb = s * fv, st = s - sb;
+                const float w_tr = st * fu, w_tl = st - w_tr;
+                const float w_br = sb * fu, w_bl = sb - w_br;
+                const bool in_l = iu >= 0, in_r = iu + 1 < isx, in_t = iv >= 0, in_b = iv + 1 < isy;
+                if (tiled) {
+                    // index in the tile; the footprint box covers every in-detector
+                    // corner, the unsigned clamp only guards the array
+                    const int q0 = (iv - p.y) * p.z + (iu - p.x);
+                    auto at = [&](int d) { return &tile[min((unsigned)(q0 + d), (unsigned)(kAdjTile - 1))]; };
+                    auto add = [&](int d, float t) {
+                        if constexpr (kAccFloat)
+                            red_shared_add(at(d), t);
+                        else if constexpr (sizeof(AdjAcc) == 8)   // two's complement add
+                            atomicAdd(reinterpret_cast<unsigned long long *>(at(d)),
+                                      (unsigned long long)__float2ll_rn(t * sc.x));
+                        else
+                            atomicAdd(at(d), __float2int_rn(t * sc.x));
+                    };
+                    if (in_t) {
+                        if (in_l) add(0, w_tl);
+                        if (in_r) add(1, w_tr);
+                    }
+                    if (in_b) {
+                        if (in_l) add(p.z, w_bl);
+                        if (in_r) add(p.z + 1, w_br);
+                    }
+                } else {
+                    const long long base = (long long)iv * isx + iu;
+                    if (in_t) {
+                        if (in_l) atomicAdd(img + base, w_tl);
+                        if (in_r) atomicAdd(img + base + 1, w_tr);
+                    }
+                    if (in_b) {
+                        if (in_l) atomicAdd(img + base + isx, w_bl);
+                        if (in_r) atomicAdd(img + base + isx + 1, w_br);
+                    }
                 }
             }
         }
@@ -328,6 +348,7 @@ cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom
     constexpr int TX = 8 * kVoxPerLane, LZ = 4;
     dim3 grid((g.L + TX - 1) / TX, (g.L + kWarpsY - 1) / kWarpsY, (g.L + LZ - 1) / LZ);
     if (smem) {
+        grid.y = (g.L + kWarpsY * kAdjVPY - 1) / (kWarpsY * kAdjVPY);
         if (ieee_rcp)
             bp_adjoint_smem_kernel<true><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
         else

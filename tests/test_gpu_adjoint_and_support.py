@@ -34,20 +34,32 @@ def test_adjoint_matches_oracle(L, scan):
     assert rel_l2(got_h, ref) <= 1e-5
 
 
-def test_adjoint_dot_product_on_gpu():
-    """<B p, f> = <p, B^T f> with both operators on the GPU (FP32)."""
+@pytest.mark.parametrize("signed", [False, True])
+def test_adjoint_dot_product_on_gpu(signed):
+    """<B p, f> = <p, B^T f> with both operators on the GPU (FP32).  With
+    nonnegative data the two sides agree to 5e-6 relative.  With zero-mean
+    data the sums cancel, and float32 rounding scales with the sum of
+    magnitudes <|p|, B^T |f|>, the bound used then."""
     scan, vol = synth.SCANS["tiny"], synth.Volume(64)
     A = oracle.carm_matrices(scan)
     rng = np.random.default_rng(21)
-    p = torch.from_numpy(rng.standard_normal((scan.n, scan.isy, scan.isx)).astype(np.float32)).cuda()
-    f = torch.from_numpy(rng.standard_normal((vol.L,) * 3).astype(np.float32)).cuda()
+    draw = rng.standard_normal if signed else rng.random
+    p = torch.from_numpy(draw((scan.n, scan.isy, scan.isx)).astype(np.float32)).cuda()
+    f = torch.from_numpy(draw((vol.L,) * 3).astype(np.float32)).cuda()
     with make_bp(vol, scan) as bp:
         bp.add_projections(p, A)
         Bp = bp.finalize()
         Btf = bp.adjoint(f, A)
+        Bt_abs = bp.adjoint(f.abs(), A)
     lhs = float((Bp.double() * f.double()).sum())
     rhs = float((p.double() * Btf.double()).sum())
-    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    magnitude = float((p.double().abs() * Bt_abs.double()).sum())
+    print(f"dot product ({'signed' if signed else 'nonnegative'}): |lhs - rhs| / |lhs| {abs(lhs - rhs) / abs(lhs):.2e}, "
+          f"/ <|p|, B^T|f|> {abs(lhs - rhs) / magnitude:.2e}")
+    if signed:
+        assert abs(lhs - rhs) <= 1e-5 * magnitude
+    else:
+        assert abs(lhs - rhs) <= 5e-6 * abs(lhs)
 
 
 def test_adjoint_of_half_detector_workload_sampled():
@@ -167,8 +179,12 @@ def test_gpu_fdk_chain_matches_oracle_chain():
     (48, synth.Scan(n=20, isx=24, isy=10, pitch=4.0)),      # detector sees part of the volume
 ])
 def test_shared_memory_adjoint_matches_direct_and_oracle(L, scan):
-    """The shared-memory adjoint (default) and the direct-atomic one give the
-    same images up to float32 summation order, and both match the oracle."""
+    """The shared-memory adjoint (default) and the direct-atomic one agree
+    to 5e-6 and both match the oracle to 1e-5.  The direct kernel's images
+    differ from the oracle by float32 summation order.  The tile kernel's
+    also differ by its fixed-point quantisation: a term is rounded to 2^-31
+    of the block's bound sum(|f|) max(r^2), about 1e-6 relative on these
+    coarse detectors."""
     api = native()
     from paper_1104_5243_gb300 import _native as N
     vol = synth.Volume(L)
@@ -180,7 +196,7 @@ def test_shared_memory_adjoint_matches_direct_and_oracle(L, scan):
         with make_bp(vol, scan) as bp:
             bp.set_option(N.BP_OPT_CULL, cull)
             outs.append(bp.adjoint(torch.from_numpy(f).cuda(), A).cpu().numpy())
-    assert rel_l2(outs[1], outs[0]) <= 1e-6
+    assert rel_l2(outs[1], outs[0]) <= 5e-6
     for o in outs:
         assert rel_l2(o, ref) <= 1e-5
 
