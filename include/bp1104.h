@@ -90,23 +90,29 @@ typedef enum {
      * misses the detector (the line-wise clipping of Sect. 3.3 at block
      * granularity; the skipped terms are exactly zero, so the volume is
      * bit-identical); 0: compute every term.  For bp_adjoint, 1 also
-     * accumulates each block's footprint in shared memory before adding it
-     * to the images (fewer global atomics; same sums up to float32 order). */
+     * accumulates each block's footprint in a shared-memory tile (32-bit
+     * fixed point, scaled per block and projection so that no sum can
+     * overflow) before adding it to the images with one atomic per pixel;
+     * 0 uses float32 global atomics per update (the sums agree to about
+     * 1e-6). */
     BP_OPT_CULL = 6,
     /* Host float32 images with the texture path: 1 (default) copy-engine
      * transfers straight into the arrays, image by image; 0 one linear
      * host-to-device copy per batch into a staging buffer, then a copy
      * kernel into the arrays. */
     BP_OPT_HOST_DIRECT = 7,
-    /* BP_F32 projections: 1 (default) centre the detector coordinates per
-     * block of voxels (the texture kernel's thread block, or the TMA path's
-     * 32x16x8 brick) and projection, 0 once per projection.  Per-block
-     * centring costs a pre-pass and 2 x 48 bytes of device memory per (block,
-     * projection of a batch) (768 MiB for a 512^3 volume on the texture path,
-     * 192 MiB on the TMA path), and cuts the float32 rounding of u and v by
-     * the ratio of block to volume footprint (rel-L2 5e-7 instead of 1e-5 on
-     * a full 1248x960 detector).  16-bit storage always centres per
-     * projection. */
+    /* 1 (default): centre the detector coordinates per block of voxels and
+     * projection, 0: once per projection.  Applies to BP_F32 projections in
+     * bp_add_projections (blocks: the texture kernel's thread block or the
+     * TMA path's 32x16x8 brick) and to bp_adjoint's shared-tile kernel
+     * (32x32x4 blocks; BP_OPT_CULL 1).  Per-block centring costs a pre-pass
+     * and 48 bytes of device memory per (block, projection of a batch), per
+     * input set for bp_add_projections (768 MiB for a 512^3 volume on the
+     * texture path, 192 MiB on the TMA path, 96 MiB for the adjoint), and
+     * cuts the float32 rounding of u and v by the ratio of block to volume
+     * footprint (rel-L2 5e-7 instead of 1e-5 for the backprojection on a
+     * full 1248x960 detector, 6e-7 instead of 4e-6 for the adjoint).  16-bit
+     * storage always centres per projection. */
     BP_OPT_BLOCK_CENTRE = 8
 } bp_option;
 

@@ -140,12 +140,19 @@ __device__ __forceinline__ void red_shared_add(float *p, float v)
 // its tile, barriers) is spread over 4096 updates.
 constexpr int kAdjVPY = 4;
 
-template <bool IEEE>
+// BLK: per-block centring, as in the forward kernels: the block stages its
+// centring records of the batch (u row, v row, (w_c, ku_b, kv_b); written by
+// the per-tile pre-pass with this kernel's block as the tile) and works
+// with offsets from the centre of its voxel box, so u and v stay within the
+// block's footprint.  The records centre u' = u - ku_b + 1; the kernel's
+// pixel offsets are ku_b - 1, kv_b - 1.
+template <bool IEEE, bool BLK>
 __global__ void __launch_bounds__(kThreads)
 bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restrict__ vol, const VolGeom g,
                        float *__restrict__ out, int isx, int isy)
 {
     constexpr int LX = 8, LZ = 32 / LX, TX = LX * kVoxPerLane, TY = kWarpsY * kAdjVPY;
+    static_assert(TX == kAdjBlockX && TY == kAdjBlockY && LZ == kAdjBlockZ, "pre-pass tile must be the block");
     __shared__ __align__(16) AdjAcc tile[kAdjTile];
     // (x0, y0, W, H); W = 0 culled, W < 0 too large.  Two slots: warp 0
     // writes the next projection's plan while slower warps may still read
@@ -153,6 +160,7 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
     __shared__ int4 plan[2];
     __shared__ float2 plan_scale[2];   // (scale, 1 / scale) of the fixed-point tile
     __shared__ float fsum_warp[kThreads / 32];
+    __shared__ float4 rec[3][BLK ? kMaxBatch : 1];
     const int lane = threadIdx.x & 31;
     const int tx = lane % LX, tz = lane / LX;
     const int L = g.L;
@@ -161,22 +169,35 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
     const int yb = by0 + (threadIdx.x >> 5);   // this lane's rows: yb + kWarpsY * ky
     const int z = bz0 + tz;
 
+    // voxel coordinates: absolute, or with BLK offsets from the centre of the
+    // block's voxel box clipped to the volume ((x0 + x1) / 2 etc., a multiple
+    // of 1/2, as in the pre-pass)
+    const int xe = min(bx0 + TX, L) - 1, ye = min(by0 + TY, L) - 1, ze = min(bz0 + LZ, L) - 1;
+    const float hx = 0.5f * (float)(bx0 + xe), hy = 0.5f * (float)(by0 + ye), hz = 0.5f * (float)(bz0 + ze);
     float f[kAdjVPY][kVoxPerLane], X[kVoxPerLane], Y[kAdjVPY];
 #pragma unroll
     for (int k = 0; k < kVoxPerLane; ++k)
-        X[k] = fmaf(g.R, (float)(xb + LX * k), g.Ox);
+        X[k] = BLK ? g.R * ((float)(xb + LX * k) - hx) : fmaf(g.R, (float)(xb + LX * k), g.Ox);
 #pragma unroll
     for (int ky = 0; ky < kAdjVPY; ++ky) {
         const int y = yb + kWarpsY * ky;
         const bool live = y < L && z < L;
-        Y[ky] = fmaf(g.R, (float)y, g.Oy);
+        Y[ky] = BLK ? g.R * ((float)y - hy) : fmaf(g.R, (float)y, g.Oy);
 #pragma unroll
         for (int k = 0; k < kVoxPerLane; ++k) {
             const int x = xb + LX * k;
             f[ky][k] = (live && x < L) ? vol[((size_t)z * L + y) * L + x] : 0.f;
         }
     }
-    const float Z = fmaf(g.R, (float)z, g.Oz);
+    const float Z = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)z, g.Oz);
+    if constexpr (BLK) {
+        if (threadIdx.x < 3 * kMaxBatch) {
+            const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            const int part = threadIdx.x / kMaxBatch, i = threadIdx.x % kMaxBatch;
+            if (i < b.n)
+                rec[part][i] = b.centres[((size_t)part * kMaxBatch + i) * b.blocks + blk];
+        }
+    }
     // sum of |f| over the block, for the fixed-point scale (rounded up by
     // the factor applied to B below)
     float fm = 0.f;
@@ -195,7 +216,6 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
     for (int w8 = 0; w8 < kThreads / 32; ++w8)
         fsum_blk += fsum_warp[w8];
     // corner of the block's voxel box taken by lane c < 8 of warp 0
-    const int xe = min(bx0 + TX, L) - 1, ye = min(by0 + TY, L) - 1, ze = min(bz0 + LZ, L) - 1;
     const float CX = fmaf(g.R, (float)((lane & 1) ? xe : bx0), g.Ox);
     const float CY = fmaf(g.R, (float)((lane & 2) ? ye : by0), g.Oy);
     const float CZ = fmaf(g.R, (float)((lane & 4) ? ze : bz0), g.Oz);
@@ -262,26 +282,36 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
                 reinterpret_cast<int4 *>(tile)[q] = make_int4(0, 0, 0, 0);
             __syncthreads();
         }
-        const float ulo = (float)(-1 - kc.x), uhi = (float)(isx - kc.x);
-        const float vlo = (float)(-1 - kc.y), vhi = (float)(isy - kc.y);
+        // the voxels' rows and pixel offsets: the projection's (the plan
+        // above), or with BLK the block's recentred ones
+        float4 vu = ru, vv = rv, vw4 = rw;
+        int2 kb = kc;
+        if constexpr (BLK) {
+            vu = rec[0][i];
+            vv = rec[1][i];
+            vw4.w = rec[2][i].x;
+            kb = make_int2((int)rec[2][i].y - 1, (int)rec[2][i].z - 1);
+        }
+        const float ulo = (float)(-1 - kb.x), uhi = (float)(isx - kb.x);
+        const float vlo = (float)(-1 - kb.y), vhi = (float)(isy - kb.y);
 #pragma unroll
         for (int ky = 0; ky < kAdjVPY; ++ky) {
-            const float bu = fmaf(ru.y, Y[ky], fmaf(ru.z, Z, ru.w));
-            const float bv = fmaf(rv.y, Y[ky], fmaf(rv.z, Z, rv.w));
-            const float bw = fmaf(rw.y, Y[ky], fmaf(rw.z, Z, rw.w));
+            const float bu = fmaf(vu.y, Y[ky], fmaf(vu.z, Z, vu.w));
+            const float bv = fmaf(vv.y, Y[ky], fmaf(vv.z, Z, vv.w));
+            const float bw = fmaf(vw4.y, Y[ky], fmaf(vw4.z, Z, vw4.w));
 #pragma unroll
             for (int k = 0; k < kVoxPerLane; ++k) {
                 if (f[ky][k] == 0.f)
                     continue;
-                const float uw = fmaf(ru.x, X[k], bu);
-                const float vw = fmaf(rv.x, X[k], bv);
-                const float w = fmaf(rw.x, X[k], bw);
+                const float uw = fmaf(vu.x, X[k], bu);
+                const float vw = fmaf(vv.x, X[k], bv);
+                const float w = fmaf(vw4.x, X[k], bw);
                 const float r = recip_adj<IEEE>(w);
                 const float u = uw * r, v = vw * r;
                 if (!(u > ulo && u < uhi && v > vlo && v < vhi))
                     continue;
                 const float fu0 = floorf(u), fv0 = floorf(v);
-                const int iu = (int)fu0 + kc.x, iv = (int)fv0 + kc.y;
+                const int iu = (int)fu0 + kb.x, iv = (int)fv0 + kb.y;
                 const float fu = u - fu0, fv = v - fv0;
                 const float s = f[ky][k] * (r * r);
                 const float sb = s * fv, st = s - sb;
@@ -349,10 +379,16 @@ cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom
     dim3 grid((g.L + TX - 1) / TX, (g.L + kWarpsY - 1) / kWarpsY, (g.L + LZ - 1) / LZ);
     if (smem) {
         grid.y = (g.L + kWarpsY * kAdjVPY - 1) / (kWarpsY * kAdjVPY);
-        if (ieee_rcp)
-            bp_adjoint_smem_kernel<true><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
-        else
-            bp_adjoint_smem_kernel<false><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
+        if (b.centres) {
+            if (ieee_rcp)
+                bp_adjoint_smem_kernel<true, true><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
+            else
+                bp_adjoint_smem_kernel<false, true><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
+        } else if (ieee_rcp) {
+            bp_adjoint_smem_kernel<true, false><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
+        } else {
+            bp_adjoint_smem_kernel<false, false><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
+        }
     } else if (ieee_rcp) {
         bp_adjoint_kernel<true><<<grid, kThreads, 0, s>>>(b, vol, g, out, isx, isy);
     } else {

@@ -90,6 +90,8 @@ struct bp_ctx {
     long long centre_blocks[2] = {0, 0};
     int4 *boxes[2] = {nullptr, nullptr};   // TMA path: per-(brick, projection) box decisions
     long long box_bricks[2] = {0, 0};
+    float4 *adj_centres = nullptr;         // adjoint: per-(block, projection) centring records
+    long long adj_blocks = 0;
     size_t ev_used = 0;
     char err[1024] = "no error";
 };
@@ -155,6 +157,8 @@ static void release(bp_ctx *c)
         if (c->boxes[s])
             cudaFree(c->boxes[s]);
     }
+    if (c->adj_centres)
+        cudaFree(c->adj_centres);
     if (c->work_dev)
         cudaFree(c->work_dev);
     if (c->copy_stream)
@@ -778,10 +782,30 @@ extern "C" bp_status bp_adjoint(bp_ctx *c, const float *vol, int vol_on_device, 
     if (e == cudaSuccess)
         e = cudaMemsetAsync(dout, 0, sizeof(float) * img_elems * n, c->stream);
     const VolGeom g = vol_geom(c);
+    // The shared-tile kernel (BP_OPT_CULL) centres per block with
+    // BP_OPT_BLOCK_CENTRE: its records come from the per-tile pre-pass, on
+    // this stream, with the kernel's block as the tile.
+    const bool blk = c->cull && c->block_centre;
+    const long long nb = tile_count(c->L, kAdjBlockX, kAdjBlockY, kAdjBlockZ);
+    if (e == cudaSuccess && blk && nb > c->adj_blocks) {
+        if (c->adj_centres)
+            e = cudaFree(c->adj_centres);
+        c->adj_centres = nullptr;
+        c->adj_blocks = 0;
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&c->adj_centres, sizeof(float4) * 3 * kMaxBatch * nb);
+        if (e == cudaSuccess)
+            c->adj_blocks = nb;
+    }
     for (int c0 = 0; e == cudaSuccess && c0 < n; c0 += kMaxBatch) {
         const int m = n - c0 < kMaxBatch ? n - c0 : kMaxBatch;
         AdjBatch b;
         b.n = m;
+        b.centres = nullptr;
+        b.blocks = nb;
+        FwdBatch fb;   // the same rows in the forward convention, for the pre-pass
+        fb.n = m;
+        double rows[kMaxBatch][3][4];
         for (int j = 0; j < m; ++j) {
             const double *a = A + 12 * (size_t)(c0 + j);
             double ku, kv;
@@ -791,8 +815,27 @@ extern "C" bp_status bp_adjoint(bp_ctx *c, const float *vol, int vol_on_device, 
             b.m[j][2] = row4(a, 2, 0.0);
             b.k[j] = make_int2((int)ku, (int)kv);
             b.out_off[j] = (long long)(c0 + j) * (long long)img_elems;
+            if (blk) {
+                fb.m[j][0] = row4(a, 0, 1.0 - ku);
+                fb.m[j][1] = row4(a, 1, 1.0 - kv);
+                fb.m[j][2] = row4(a, 2, 0.0);
+                fb.k[j] = make_float2((float)ku, (float)kv);
+                for (int q = 0; q < 4; ++q) {
+                    rows[j][0][q] = a[q] + (1.0 - ku) * a[8 + q];
+                    rows[j][1][q] = a[4 + q] + (1.0 - kv) * a[8 + q];
+                    rows[j][2][q] = a[8 + q];
+                }
+            }
         }
-        e = launch_bp_adjoint(b, dvol, g, dout, c->isx, c->isy, c->ieee_rcp, c->cull, c->stream);
+        if (blk) {
+            CentreBatch cb;
+            centre_batch(&cb, &rows[0][0][0], m, c->O, c->R);
+            e = launch_block_prepass(fb, &cb, g, c->isx, c->isy, kAdjBlockX, kAdjBlockY, kAdjBlockZ, nullptr,
+                                     c->adj_centres, nullptr, nullptr, nullptr, c->stream);
+            b.centres = c->adj_centres;
+        }
+        if (e == cudaSuccess)
+            e = launch_bp_adjoint(b, dvol, g, dout, c->isx, c->isy, c->ieee_rcp, c->cull, c->stream);
     }
     if (e == cudaSuccess && !out_on_device) {
         e = cudaMemcpyAsync(images_out, dout, sizeof(float) * img_elems * n, cudaMemcpyDeviceToHost, c->stream);

@@ -42,8 +42,13 @@ struct AdjBatch {
     float4 m[kMaxBatch][3];
     int2 k[kMaxBatch];
     long long out_off[kMaxBatch];
+    const float4 *centres;   // per-block centring records (shared-tile kernel; NULL: per projection)
+    long long blocks;        // blocks of the volume (record plane stride)
     int n;
 };
+// The shared-tile adjoint kernel's block of voxels (the pre-pass tile for
+// its centring records).
+constexpr int kAdjBlockX = 32, kAdjBlockY = 32, kAdjBlockZ = 4;
 
 struct VolGeom {
     int L;

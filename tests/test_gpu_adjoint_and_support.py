@@ -228,3 +228,18 @@ def test_adjoint_full_detector_512(kind):
     err_abs = np.linalg.norm(got - ref) / scale
     print(f"adjoint 512^3 -> 4 x 1248x960 {kind}: rel-L2 {err:.3e}, against B^T|f| {err_abs:.3e}")
     assert err_abs <= 1e-5
+
+
+def test_adjoint_oversized_footprints_use_global_atomics():
+    """256^3 (1 mm voxels, about 5 detector pixels each) onto the full
+    1248x960 detector: a 32 x 32 x 4-voxel block's footprint spans 3700-5200
+    pixels, more than the shared tile holds, so the tile kernel takes its
+    global-atomic branch (with per-block centring)."""
+    scan = synth.Scan(n=6, isx=1248, isy=960, pitch=0.308)
+    vol = synth.Volume(256)
+    A = oracle.carm_matrices(scan)
+    f = synth.uniform_volume(vol.L, seed=33) - 0.25
+    ref = oracle.adjoint(vol.L, vol.R, vol.O, f.astype(np.float64), A, scan.isx, scan.isy)
+    with make_bp(vol, scan) as bp:
+        got = bp.adjoint(torch.from_numpy(f).cuda(), A).cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-5
