@@ -49,16 +49,20 @@ UNIT = "GUP/s"
 #   gather: the texture unit's 2x2-gather rate for the storage type, MEASURED
 #     on this GPU by bp_probe_gather (one gather per update).
 # TMA kernel (bp_tma_kernel):
-#   smem: 128 B per SM per clock of shared-memory bandwidth over 24.0 B per
-#     update: two 8-byte pair loads, plus the TMA fill of the 114 x 36-pair box
-#     (32832 B) per 32 x 16 x 8-voxel brick and projection.
+#   smem: 128 B per SM per clock of shared-memory bandwidth over the bytes an
+#     update moves: two pair loads (8-byte float32 pairs, 4-byte 16-bit ones),
+#     plus the TMA fill of the box (114 x 36 float32 pairs, 100 x 36 16-bit
+#     ones) per 32 x 16 x 8-voxel brick and projection: 24.0 B (f32), 11.5 B.
 FP32_PER_SM_CLK = 128.0
 FP32_INSTR_PER_UPDATE = 20.5
 ISSUE_PER_SM_CLK = 128.0
-INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 28.7}
+INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 28.7, ("tma", "f16"): 34.6,
+                    ("tma", "bf16"): 34.6}
 MUFU_PER_SM_CLK = 16.0
 SMEM_BYTES_PER_SM_CLK = 128.0
-TMA_SMEM_BYTES_PER_UPDATE = 16.0 + 114 * 36 * 8 / (32 * 16 * 8)
+def tma_smem_bytes_per_update(form: str) -> float:
+    pair, bu = (8, 114) if form == "f32" else (4, 100)
+    return 2.0 * pair + bu * 36 * pair / (32 * 16 * 8)
 
 
 def roofline_peak_gups(path: str, form: str, sm_mhz: float, sms: int, gather_per_sm_clk: float) -> dict:
@@ -68,7 +72,7 @@ def roofline_peak_gups(path: str, form: str, sm_mhz: float, sms: int, gather_per
         "mufu": sms * MUFU_PER_SM_CLK * f / 1e9,
     }
     if path == "tma":
-        bounds["smem"] = sms * SMEM_BYTES_PER_SM_CLK / TMA_SMEM_BYTES_PER_UPDATE * f / 1e9
+        bounds["smem"] = sms * SMEM_BYTES_PER_SM_CLK / tma_smem_bytes_per_update(form) * f / 1e9
     else:
         bounds["gather"] = sms * gather_per_sm_clk * f / 1e9
     instr = INSTR_PER_UPDATE.get((path, form))
@@ -282,6 +286,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--L", type=int, default=512)
     ap.add_argument("--forms", default="f32,f16,bf16")
+    ap.add_argument("--path", default="auto", choices=["auto", "texture", "tma"],
+                    help="data path of the backprojection (profiling runs; default: the library's choice)")
     ap.add_argument("--n-proj", type=int, default=496, help="projections per step (profiling runs)")
     ap.add_argument("--cpu-proj", type=int, default=128, help="projections in the oracle sample")
     ap.add_argument("--ref-proj", type=int, default=48, help="projections per reference-arm step")
@@ -342,6 +348,7 @@ def main():
     clocks = None
     for form in args.forms.split(","):
         bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=form)
+        bp.set_option(N.BP_OPT_PATH, {"auto": 0, "texture": 1, "tma": 2}[args.path])
 
         def step():
             bp.reset()

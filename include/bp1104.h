@@ -80,10 +80,11 @@ typedef enum {
     /* Data path of the backprojection: 0 (default) automatic, 1 texture
      * gathers, 2 TMA-staged shared-memory tiles.  With the same centring
      * (BP_F16 / BP_BF16, or BP_OPT_BLOCK_CENTRE 0) the two give
-     * bit-identical volumes.  The automatic choice is the faster on GB300:
-     * the TMA path for BP_F32 projections, the texture path (with
-     * BP_OPT_CULL) for BP_F16 / BP_BF16.  The TMA path allocates two sets of
-     * 64 pair images on first use (1.2 GB for 1248x960 BP_F32).
+     * bit-identical volumes.  The automatic choice is the TMA path, the
+     * faster on GB300 for every storage type (most for BP_F32, whose 32-bit
+     * texture gathers the texture unit returns at half the 16-bit rate).
+     * The TMA path allocates two sets of 64 pair images on first use (1.2 GB
+     * for 1248x960 BP_F32, 0.6 GB for 16-bit storage).
      * bp_query(BP_QUERY_LAST_PATH) reports the path taken. */
     BP_OPT_PATH = 5,
     /* 1 (default): skip, per block of voxels, the projections whose footprint

@@ -473,11 +473,10 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
         const int m = n - c0 < c->batch ? n - c0 : c->batch;
         const double *A0 = A + 12 * (size_t)c0;
         // Automatic choice, by measurement on GB300 (512^3 x 1248x960): the
-        // TMA path for float32 projections (the texture unit returns 32-bit
-        // gathers at half the 16-bit rate, which bounds the texture kernel;
-        // 1148 against 801 GUP/s), the texture path for 16-bit storage (1240
-        // against 1132).
-        const bool tma = c->path == 2 || (c->path == 0 && c->dtype == BP_F32);
+        // TMA path for every storage type (f32 1313 against 801 GUP/s: the
+        // texture unit's data return bounds 32-bit gathers; bf16 1249
+        // against 1198; f16 1220-1270 against 1240).
+        const bool tma = c->path != 1;
         if (tma) {
             st = ensure_pairs(c);
             if (st != BP_OK)

@@ -301,10 +301,9 @@ def test_tma_global_fallback_when_footprints_exceed_the_tile():
     assert rel_l2(blk.view(-1).numpy()[idx], ref) <= FP32_TOL
 
 
-@pytest.mark.parametrize("dtype,expect", [("f32", "tma"), ("f16", "texture"), ("bf16", "texture")])
+@pytest.mark.parametrize("dtype,expect", [("f32", "tma"), ("f16", "tma"), ("bf16", "tma")])
 def test_automatic_path_choice(dtype, expect):
-    """Automatic: the TMA path for float32 projections, the texture path for
-    16-bit storage (the faster of the two for each on GB300)."""
+    """Automatic: the TMA path, the faster on GB300 for every storage type."""
     scan = synth.SCANS["full"]
     A = oracle.carm_matrices(scan)[:8]
     q = synth.uniform_stack(8, scan.isy, scan.isx, seed=3)
