@@ -115,9 +115,10 @@ def ncu_traffic(kernel_file: str, profile: str):
         return None
     fields = {}
     for ln in text.splitlines():
-        if ":" in ln and ln.strip().startswith(("traffic_bytes_per_launch", "source_sha256")):
-            k, v = ln.split(":", 1)
-            fields[k.strip("-* `")] = v.strip().strip("`")
+        item = ln.strip().lstrip("-* ").strip()   # "- name: value" list items
+        if ":" in item and item.startswith(("traffic_bytes_per_launch", "source_sha256")):
+            k, v = item.split(":", 1)
+            fields[k.strip("` ")] = v.strip().strip("`")
     if fields.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
     try:

@@ -57,3 +57,17 @@ def test_reference_arm_prints_only_on_rank_zero():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "GUP/s" and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+
+
+def test_ncu_traffic_reads_the_committed_summary():
+    """The roofline's traffic comes from the committed ncu summary of the
+    default kernel while its source is unchanged (the summary records the
+    source's sha256)."""
+    import hashlib
+    import bench
+    src = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1104_5243_gb300", "csrc",
+                       "bp_tma.cu")
+    text = open(os.path.join(os.path.dirname(src), "..", "..", "profiles", "bp_tma_kernel_f32_512.md")).read()
+    current = hashlib.sha256(open(src, "rb").read()).hexdigest() in text
+    t = bench.ncu_traffic("bp_tma.cu", "bp_tma_kernel_f32_512.md")
+    assert (t is not None and t > 1e9) if current else t is None
