@@ -209,6 +209,16 @@ bp_status bp_kernel_stats(bp_ctx *ctx, long long *launches, double *total_ms);
  * array). */
 bp_status bp_probe_gather(bp_dtype dtype, double *gathers_per_sm_clk);
 
+/* Self-test of the failure detection of the TMA path's device-side waits (no
+ * counterpart in the paper).  One warp waits, with the bounded wait the
+ * backprojection kernel uses, on a barrier that is completed (arrive = 1)
+ * or that nothing completes (arrive = 0), at most iters (1 .. 2^20)
+ * suspensions of 100 us each.  Returns BP_OK when the wait succeeded and
+ * BP_ETIMEOUT when it gave up; nothing faults or hangs, and the device stays
+ * usable.  BP_EINVAL for bad arguments (checked before any CUDA call).
+ * Synchronous, on the current device. */
+bp_status bp_selftest_bounded_wait(int arrive, int iters);
+
 /* Message of the last failure on ctx (or, for ctx == NULL, of the calling
  * thread's last failing context-free call).  Never NULL. */
 const char *bp_last_error(const bp_ctx *ctx);

@@ -31,6 +31,7 @@ SIGNATURES = {
     "bp_kernel_stats": (_i, [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_d)]),
     "bp_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "bp_probe_gather": (_i, [_i, ctypes.POINTER(_d)]),
+    "bp_selftest_bounded_wait": (_i, [_i, _i]),
     "bp_last_error": (ctypes.c_char_p, [_vp]),
     "bp_carm_matrices": (_i, [_i, _vp, _d, _d, _d, _d, _d, _vp, _vp]),
     "bp_ellipsoid_project": (_i, [_i, _vp, _i, _i, _i, _vp, _vp, _vp]),
@@ -145,6 +146,15 @@ def bp_probe_gather(dtype) -> float:
     r = _d(0.0)
     check(lib().bp_probe_gather(int(dtype), ctypes.byref(r)))
     return r.value
+
+
+def bp_selftest_bounded_wait(arrive: bool, iters: int) -> int:
+    """Status of the bounded-wait self-test (BP_OK or BP_ETIMEOUT; other
+    statuses raise)."""
+    st = lib().bp_selftest_bounded_wait(int(bool(arrive)), int(iters))
+    if st not in (BP_OK, BP_ETIMEOUT):
+        check(st)
+    return st
 
 
 def bp_last_error(ctx=None) -> str:

@@ -83,10 +83,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return done != 0;
 }
 
-// Bounded wait: at most kTmaWaitIters suspensions of kTmaSuspendNs each.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Bounded wait: at most iters suspensions of kTmaSuspendNs each.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int iters = kTmaWaitIters)
 {
-    for (int it = 0; it < kTmaWaitIters; ++it)
+    for (int it = 0; it < iters; ++it)
         if (mbar_try_wait(bar, parity))
             return true;
     return false;
@@ -525,4 +525,54 @@ cudaError_t launch_pair_images(const PairBatch &b, int isx, int isy, int pitch, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Self-test of the bounded wait (failure detection without a GPU fault): one
+// warp waits, with the backprojection kernel's helper, on an mbarrier that
+// lane 0 completes (arrive) or that nothing completes; after iters
+// suspensions the wait gives up, and lane 0 records the error flag the host
+// turns into BP_ETIMEOUT, as the backprojection kernel does.
+__global__ void __launch_bounds__(32) wait_selftest_kernel(int arrive, int iters, int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (arrive && threadIdx.x == 0)
+        mbar_arrive(&bar);
+    __syncwarp();
+    if (!mbar_wait_bounded(&bar, 0, iters) && threadIdx.x == 0)
+        atomicExch(err, 1);
+}
+
 }  // namespace bp
+
+extern "C" bp_status bp_selftest_bounded_wait(int arrive, int iters)
+{
+    if ((arrive != 0 && arrive != 1) || iters < 1 || iters > (1 << 20)) {
+        bp::set_thread_error("bp_selftest_bounded_wait: arrive must be 0 or 1 and iters in [1, 2^20]");
+        return BP_EINVAL;
+    }
+    int *err = nullptr, flag = 0;
+    cudaError_t e = cudaMalloc((void **)&err, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        bp::wait_selftest_kernel<<<1, 32>>>(arrive, iters, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err)
+        cudaFree(err);
+    if (e != cudaSuccess) {
+        bp::set_thread_error("bp_selftest_bounded_wait: %s", cudaGetErrorString(e));
+        return BP_ECUDA;
+    }
+    if (flag) {
+        bp::set_thread_error("bp_selftest_bounded_wait: the wait gave up after %d suspensions", iters);
+        return BP_ETIMEOUT;
+    }
+    return BP_OK;
+}

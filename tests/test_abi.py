@@ -81,3 +81,10 @@ def test_context_free_calls_validate_arguments(lib):
     assert lib.bp_ramp_filter(0, 16, 1.0, None, None, None) == N.BP_OK
     assert lib.bp_row_filter_fwd(0, 16, 8, None, None, None, None) == N.BP_OK
     assert lib.bp_carm_matrices(0, None, 785.0, 1200.0, 1.0, 0.0, 0.0, None, None) == N.BP_OK
+
+
+def test_bounded_wait_selftest_validates_arguments_without_the_gpu(lib):
+    assert lib.bp_selftest_bounded_wait(2, 10) == N.BP_EINVAL
+    assert lib.bp_selftest_bounded_wait(0, 0) == N.BP_EINVAL
+    assert lib.bp_selftest_bounded_wait(1, (1 << 20) + 1) == N.BP_EINVAL
+    assert "bp_selftest_bounded_wait" in N.bp_last_error(None)
