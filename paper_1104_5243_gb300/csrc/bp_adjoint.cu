@@ -12,8 +12,6 @@
 // (neighbouring voxels land 1..5 pixels apart), so same-address conflicts
 // inside a warp are rare and contention is across warps and blocks, along
 // the rays.
-#include <type_traits>
-
 #include "bp_internal.cuh"
 
 namespace bp {
@@ -126,12 +124,6 @@ bp_adjoint_kernel(const __grid_constant__ AdjBatch b, const float *__restrict__ 
 // Same coordinates and weights as bp_adjoint_kernel.
 using AdjAcc = int;
 constexpr int kAccBits = 8 * (int)sizeof(AdjAcc);
-constexpr bool kAccFloat = std::is_same<AdjAcc, float>::value;
-
-__device__ __forceinline__ void red_shared_add(float *p, float v)
-{
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
-}
 
 // Blocks of 32 x 32 x 4 voxels: each lane takes 4 voxels along x (8 apart)
 // and kAdjVPY along y (one per warp row, kWarpsY apart).  A block's
@@ -276,8 +268,7 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
         const bool tiled = p.z > 0;
         if (tiled) {
             // kAdjTile is a multiple of 4: zero whole 16-byte words covering W * H
-            constexpr int kPer16 = 16 / (int)sizeof(AdjAcc);
-            const int n16 = (p.z * p.w + kPer16 - 1) / kPer16;
+            const int n16 = (p.z * p.w + 3) / 4;   // four int32 per 16-byte word
             for (int q = threadIdx.x; q < n16; q += kThreads)
                 reinterpret_cast<int4 *>(tile)[q] = make_int4(0, 0, 0, 0);
             __syncthreads();
@@ -323,15 +314,7 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
                     // corner, the unsigned clamp only guards the array
                     const int q0 = (iv - p.y) * p.z + (iu - p.x);
                     auto at = [&](int d) { return &tile[min((unsigned)(q0 + d), (unsigned)(kAdjTile - 1))]; };
-                    auto add = [&](int d, float t) {
-                        if constexpr (kAccFloat)
-                            red_shared_add(at(d), t);
-                        else if constexpr (sizeof(AdjAcc) == 8)   // two's complement add
-                            atomicAdd(reinterpret_cast<unsigned long long *>(at(d)),
-                                      (unsigned long long)__float2ll_rn(t * sc.x));
-                        else
-                            atomicAdd(at(d), __float2int_rn(t * sc.x));
-                    };
+                    auto add = [&](int d, float t) { atomicAdd(at(d), __float2int_rn(t * sc.x)); };
                     if (in_t) {
                         if (in_l) add(0, w_tl);
                         if (in_r) add(1, w_tr);
@@ -362,7 +345,7 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
                 for (int col = lane; col < p.z; col += 32) {
                     const AdjAcc v = src[col];
                     if (v != 0)
-                        atomicAdd(dst + col, kAccFloat ? (float)v : (float)v * sc.y);
+                        atomicAdd(dst + col, (float)v * sc.y);
                 }
             }
         }

@@ -201,12 +201,6 @@ long long tile_count(int L, int tx, int ty, int tz)
     return (long long)((L + tx - 1) / tx) * ((L + ty - 1) / ty) * ((L + tz - 1) / tz);
 }
 
-long long fwd_blocks(int L, int lanes_x)
-{
-    int tx, ty, tz;
-    fwd_tile(lanes_x, &tx, &ty, &tz);
-    return tile_count(L, tx, ty, tz);
-}
 
 template <int KIND, bool IEEE, int LX, int LY, int VPL = kVoxPerLane>
 static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bool acc,

@@ -94,17 +94,17 @@ cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int t
                           bool accumulate, bool ieee_rcp, int lanes_x, const unsigned long long *masks,
                           const float4 *centres, cudaStream_t s);
 
-// Number of thread blocks of the texture kernel for a layout, and the
-// per-block pre-pass (one thread per block):
-// - masks (if not NULL): a block's bit for projection i is cleared when the
+// The per-tile pre-pass (one thread per tile of voxels: the texture
+// kernel's block, fwd_tile of its layout; the TMA path's brick; the tile
+// adjoint's block), writing for every projection of the batch
+// - masks (if not NULL): a tile's bit for projection i is cleared when the
 //   projections of its voxel box miss the detector by more than a pixel
 //   (every term of those updates is exactly zero);
-// - centres (if not NULL, with cb): the block centring records;
+// - centres (if not NULL, with cb): the tile's centring records;
+// - boxes (if not NULL, with box): the TMA path's box decisions (below);
 // - work (if not NULL): the kept updates are added to *work.
-// The pre-pass works on any tile of voxels: the texture kernel's block
-// (fwd_tile of its layout) or the TMA path's brick.
+// tile_count: tiles of an L^3 volume.
 void fwd_tile(int lanes_x, int *tx, int *ty, int *tz);
-long long fwd_blocks(int L, int lanes_x);
 long long tile_count(int L, int tx, int ty, int tz);
 // TMA-path box decision per (brick, projection), made by the pre-pass
 // (boxes, one int4 per pair at index projection * bricks + brick):
