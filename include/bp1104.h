@@ -139,6 +139,19 @@ typedef enum {
 bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
                     int isx, int isy, bp_dtype proj_dtype, void *cuda_stream);
 
+/* Like bp_create, for a z-slab of the L^3 grid: the context's volume is the
+ * nz slices z0 .. z0 + nz - 1 of the grid (L x L x nz voxels, x fastest;
+ * 1 <= nz, 0 <= z0 <= L - nz).  O is still the centre of the grid's voxel
+ * (0,0,0).  Every call on the context (bp_add_projections, bp_finalize,
+ * bp_get_state / bp_set_state, bp_adjoint, which reads an L x L x nz
+ * volume) then works on the slab alone.  Slabs reconstruct a volume larger
+ * than one context can hold (each slab takes every projection; the paper's
+ * split of the z loop, Sect. 6), or split one volume across GPUs.
+ * bp_create(L, ...) is bp_create_slab(L, L, 0, ...).  Other errors as
+ * bp_create. */
+bp_status bp_create_slab(bp_ctx **out, int L, int nz, int z0, double R, const double O[3],
+                         int isx, int isy, bp_dtype proj_dtype, void *cuda_stream);
+
 /* Release everything the context owns (synchronises its stream first).
  * NULL is accepted and ignored. */
 bp_status bp_destroy(bp_ctx *ctx);

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "BP_OK", 1: "BP_EINVAL", 2: "BP_ENOMEM", 3: "BP_ECUDA", 4: "B
 _vp, _i, _ll, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
 SIGNATURES = {
     "bp_create": (_i, [ctypes.POINTER(_vp), _i, _d, _vp, _i, _i, _i, _vp]),
+    "bp_create_slab": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _d, _vp, _i, _i, _i, _vp]),
     "bp_destroy": (_i, [_vp]),
     "bp_set_option": (_i, [_vp, _i, _ll]),
     "bp_reset": (_i, [_vp]),
@@ -91,6 +92,13 @@ def bp_create(L, R, O, isx, isy, dtype=BP_F32, stream=None):
     h = _vp()
     check(lib().bp_create(ctypes.byref(h), int(L), float(R), ctypes.cast(_dbl3(O), _vp),
                           int(isx), int(isy), int(dtype), stream))
+    return h.value
+
+
+def bp_create_slab(L, nz, z0, R, O, isx, isy, dtype=BP_F32, stream=None):
+    h = _vp()
+    check(lib().bp_create_slab(ctypes.byref(h), int(L), int(nz), int(z0), float(R), ctypes.cast(_dbl3(O), _vp),
+                               int(isx), int(isy), int(dtype), stream))
     return h.value
 
 

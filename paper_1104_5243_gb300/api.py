@@ -41,20 +41,38 @@ def _matrices(A) -> np.ndarray:
 
 
 class Backprojector:
-    """An L^3 volume accumulating backprojected ISX x ISY projections
-    (Sect. 3.1, Listing 1).  Owns the library context."""
+    """An L^3 volume (or, with nz and z0, the z-slab of slices z0 .. z0+nz-1
+    of the L^3 grid) accumulating backprojected ISX x ISY projections
+    (Sect. 3.1, Listing 1).  Owns the library context.  Volumes are (nz, L, L)
+    float32 tensors [z, y, x] (nz = L for the full cube)."""
 
     def __init__(self, L: int, R: float, O, isx: int, isy: int, dtype: str = "f32",
-                 stream: torch.cuda.Stream | None = None, device=None):
+                 stream: torch.cuda.Stream | None = None, device=None, nz: int | None = None, z0: int = 0):
         self.L, self.R, self.O = int(L), float(R), tuple(float(v) for v in O)
+        self.nz, self.z0 = (self.L if nz is None else int(nz)), int(z0)
         self.isx, self.isy = int(isx), int(isy)
         self.dtype = dtype
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self._stream = stream
         with torch.cuda.device(self.device):
-            self._ctx = N.bp_create(self.L, self.R, self.O, self.isx, self.isy, _DTYPES[dtype],
-                                    _stream_handle(stream))
+            if nz is None and self.z0 == 0:
+                self._ctx = N.bp_create(self.L, self.R, self.O, self.isx, self.isy, _DTYPES[dtype],
+                                        _stream_handle(stream))
+            else:
+                self._ctx = N.bp_create_slab(self.L, self.nz, self.z0, self.R, self.O, self.isx, self.isy,
+                                             _DTYPES[dtype], _stream_handle(stream))
+
+    @property
+    def shape(self):
+        return (self.nz, self.L, self.L)
+
+    def _volume(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        # the library copies nz * L * L floats: refuse a buffer of another size
+        t = _f32(t, name)
+        if t.numel() != self.nz * self.L * self.L:
+            raise ValueError(f"{name} must hold {self.nz} x {self.L} x {self.L} floats, got shape {tuple(t.shape)}")
+        return t
 
     # --------------------------------------------------------------------
     def close(self):
@@ -113,26 +131,26 @@ class Backprojector:
             self._keep = (images, A)
 
     def finalize(self, out: torch.Tensor | None = None) -> torch.Tensor:
-        """The accumulated volume as a (L, L, L) float32 CUDA tensor [z, y, x]."""
+        """The accumulated volume as a (nz, L, L) float32 CUDA tensor [z, y, x]."""
         if out is None:
-            out = torch.empty((self.L,) * 3, dtype=torch.float32, device=self.device)
-        out = _f32(out, "out")
+            out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        out = self._volume(out, "out")
         N.bp_finalize(self._ctx, _ptr(out), out.is_cuda)
         self._keep = None
         return out
 
     def get_state(self):
-        vol = torch.empty((self.L,) * 3, dtype=torch.float32, device=self.device)
+        vol = torch.empty(self.shape, dtype=torch.float32, device=self.device)
         n = N.bp_get_state(self._ctx, _ptr(vol), 1)
         return vol, n
 
     def set_state(self, vol: torch.Tensor, n_added: int):
-        vol = _f32(vol, "vol")
+        vol = self._volume(vol, "vol")
         N.bp_set_state(self._ctx, _ptr(vol), vol.is_cuda, n_added)
 
     def adjoint(self, vol: torch.Tensor, A, out: torch.Tensor | None = None) -> torch.Tensor:
         """B^T vol: (n, isy, isx) float32 CUDA tensor."""
-        vol = _f32(vol, "vol")
+        vol = self._volume(vol, "vol")
         A = _matrices(A)
         n = A.shape[0]
         if out is None:
@@ -140,6 +158,31 @@ class Backprojector:
         N.bp_adjoint(self._ctx, _ptr(vol), vol.is_cuda, ctypes.c_void_p(A.ctypes.data), n,
                      _ptr(out), out.is_cuda)
         return out
+
+
+def backproject_slabs(L: int, R: float, O, images: torch.Tensor, A, slab: int, dtype: str = "f32",
+                      out: torch.Tensor | None = None) -> torch.Tensor:
+    """Backproject into an L^3 volume held in HOST memory, slab by slab (the
+    paper's split of the z loop, Sect. 6): a context of at most `slab`
+    slices at a time takes every projection, and its slab is read back into
+    out[z0 : z0 + nz].  For volumes larger than one context can hold on the
+    device; every slab reads the projections again.  images: (n, ISY, ISX)
+    float32, host or device; out: (L, L, L) float32 host tensor (allocated
+    pinned if None)."""
+    L, slab = int(L), int(slab)
+    if slab < 1:
+        raise ValueError("slab must be >= 1")
+    if out is None:
+        out = torch.empty((L, L, L), dtype=torch.float32).pin_memory()
+    if out.is_cuda or tuple(out.shape) != (L, L, L) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous (L, L, L) float32 host tensor")
+    n, isy, isx = images.shape
+    for z0 in range(0, L, slab):
+        nz = min(slab, L - z0)
+        with Backprojector(L, R, O, isx, isy, dtype=dtype, nz=nz, z0=z0) as bp:
+            bp.add_projections(images, A)
+            bp.finalize(out[z0:z0 + nz])
+    return out
 
 
 # ------------------------------------------------------------------------

@@ -40,7 +40,7 @@ bp_adjoint_kernel(const __grid_constant__ AdjBatch b, const float *__restrict__ 
     const int xb = blockIdx.x * TX + tx;
     const int y = blockIdx.y * kWarpsY + (threadIdx.x >> 5);
     const int z = blockIdx.z * LZ + tz;
-    if (y >= L || z >= L)
+    if (y >= L || z >= g.Lz)
         return;
 
     const float *row = vol + ((size_t)z * L + y) * L;
@@ -164,7 +164,7 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
     // voxel coordinates: absolute, or with BLK offsets from the centre of the
     // block's voxel box clipped to the volume ((x0 + x1) / 2 etc., a multiple
     // of 1/2, as in the pre-pass)
-    const int xe = min(bx0 + TX, L) - 1, ye = min(by0 + TY, L) - 1, ze = min(bz0 + LZ, L) - 1;
+    const int xe = min(bx0 + TX, L) - 1, ye = min(by0 + TY, L) - 1, ze = min(bz0 + LZ, g.Lz) - 1;
     const float hx = 0.5f * (float)(bx0 + xe), hy = 0.5f * (float)(by0 + ye), hz = 0.5f * (float)(bz0 + ze);
     float f[kAdjVPY][kVoxPerLane], X[kVoxPerLane], Y[kAdjVPY];
 #pragma unroll
@@ -173,7 +173,7 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
 #pragma unroll
     for (int ky = 0; ky < kAdjVPY; ++ky) {
         const int y = yb + kWarpsY * ky;
-        const bool live = y < L && z < L;
+        const bool live = y < L && z < g.Lz;
         Y[ky] = BLK ? g.R * ((float)y - hy) : fmaf(g.R, (float)y, g.Oy);
 #pragma unroll
         for (int k = 0; k < kVoxPerLane; ++k) {
@@ -359,7 +359,7 @@ cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom
     if (b.n <= 0)
         return cudaSuccess;
     constexpr int TX = 8 * kVoxPerLane, LZ = 4;
-    dim3 grid((g.L + TX - 1) / TX, (g.L + kWarpsY - 1) / kWarpsY, (g.L + LZ - 1) / LZ);
+    dim3 grid((g.L + TX - 1) / TX, (g.L + kWarpsY - 1) / kWarpsY, (g.Lz + LZ - 1) / LZ);
     if (smem) {
         grid.y = (g.L + kWarpsY * kAdjVPY - 1) / (kWarpsY * kAdjVPY);
         if (b.centres) {

@@ -46,7 +46,7 @@ static EncodeTiledFn encode_tiled()
 using namespace bp;
 
 struct bp_ctx {
-    int L = 0;
+    int L = 0, Lz = 0;   // volume L x L x Lz (Lz < L: a z-slab of the L^3 grid)
     double R = 0, O[3] = {0, 0, 0};
     int isx = 0, isy = 0;
     bp_dtype dtype = BP_F32;
@@ -191,8 +191,8 @@ static bp_status alloc_slot(bp_ctx *c, int s, int j)
     return BP_OK;
 }
 
-extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3], int isx, int isy,
-                               bp_dtype proj_dtype, void *cuda_stream)
+static bp_status create_context(bp_ctx **out, int L, int nz, int z0, double R, const double O[3], int isx, int isy,
+                                bp_dtype proj_dtype, void *cuda_stream)
 {
     if (out == nullptr)
         return fail(nullptr, BP_EINVAL, "bp_create: out is NULL");
@@ -200,6 +200,8 @@ extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
     if (L < 1 || L > 4096 || !(R > 0) || !std::isfinite(R) || O == nullptr ||
         !std::isfinite(O[0]) || !std::isfinite(O[1]) || !std::isfinite(O[2]))
         return fail(nullptr, BP_EINVAL, "bp_create: invalid volume (1 <= L <= 4096, R > 0, finite O)");
+    if (nz < 1 || z0 < 0 || z0 > L - nz)
+        return fail(nullptr, BP_EINVAL, "bp_create_slab: the slab must satisfy 1 <= nz and 0 <= z0 <= L - nz");
     if (isx < 1 || isy < 1 || isx > 32768 || isy > 32768)
         return fail(nullptr, BP_EINVAL, "bp_create: detector size must be in [1, 32768]");
     if (proj_dtype != BP_F32 && proj_dtype != BP_F16 && proj_dtype != BP_BF16)
@@ -208,10 +210,11 @@ extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
     if (c == nullptr)
         return fail(nullptr, BP_ENOMEM, "bp_create: out of host memory");
     c->L = L;
+    c->Lz = nz;
     c->R = R;
     c->O[0] = O[0];
     c->O[1] = O[1];
-    c->O[2] = O[2];
+    c->O[2] = O[2] + R * z0;   // centre of the slab's voxel (0,0,0)
     c->isx = isx;
     c->isy = isy;
     c->dtype = proj_dtype;
@@ -233,7 +236,7 @@ extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
         check(cudaEventCreateWithFlags(&c->copy_done[s], cudaEventDisableTiming), "cudaEventCreate");
         check(cudaEventCreateWithFlags(&c->kern_done[s], cudaEventDisableTiming), "cudaEventCreate");
     }
-    const size_t nvox = (size_t)L * L * L;
+    const size_t nvox = (size_t)L * L * nz;
     check(cudaMalloc((void **)&c->vol, nvox * sizeof(float)), "cudaMalloc(volume)");
     check(cudaMalloc((void **)&c->err_dev, sizeof(int)), "cudaMalloc(error flag)");
     if (st == BP_OK)
@@ -258,6 +261,18 @@ extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
     }
     *out = c;
     return BP_OK;
+}
+
+extern "C" bp_status bp_create(bp_ctx **out, int L, double R, const double O[3], int isx, int isy,
+                               bp_dtype proj_dtype, void *cuda_stream)
+{
+    return create_context(out, L, L, 0, R, O, isx, isy, proj_dtype, cuda_stream);
+}
+
+extern "C" bp_status bp_create_slab(bp_ctx **out, int L, int nz, int z0, double R, const double O[3], int isx,
+                                    int isy, bp_dtype proj_dtype, void *cuda_stream)
+{
+    return create_context(out, L, nz, z0, R, O, isx, isy, proj_dtype, cuda_stream);
 }
 
 extern "C" bp_status bp_destroy(bp_ctx *c)
@@ -330,7 +345,7 @@ extern "C" bp_status bp_reset(bp_ctx *c)
     if (c == nullptr)
         return fail(nullptr, BP_EINVAL, "bp_reset: NULL context");
     CTX_CK(c, cudaSetDevice(c->device));
-    CTX_CK(c, cudaMemsetAsync(c->vol, 0, sizeof(float) * (size_t)c->L * c->L * c->L, c->stream));
+    CTX_CK(c, cudaMemsetAsync(c->vol, 0, sizeof(float) * (size_t)c->L * c->L * c->Lz, c->stream));
     c->vol_zero = true;
     c->n_added = 0;
     return BP_OK;
@@ -348,7 +363,7 @@ static bp_status check_matrices(bp_ctx *c, const char *who, const double *A, int
         for (int corner = 0; corner < 8; ++corner) {
             const double X = c->O[0] + c->R * ((corner & 1) ? c->L - 1 : 0);
             const double Y = c->O[1] + c->R * ((corner & 2) ? c->L - 1 : 0);
-            const double Z = c->O[2] + c->R * ((corner & 4) ? c->L - 1 : 0);
+            const double Z = c->O[2] + c->R * ((corner & 4) ? c->Lz - 1 : 0);
             const double w = a[8] * X + a[9] * Y + a[10] * Z + a[11];
             if (!(w > 0))
                 return fail(c, BP_EINVAL,
@@ -372,7 +387,7 @@ static inline float4 row4(const double *a, int r, double add_w)
 static inline void centre_offsets(const bp_ctx *c, const double *a, double *ku, double *kv)
 {
     const double h = 0.5 * (c->L - 1) * c->R;
-    const double X = c->O[0] + h, Y = c->O[1] + h, Z = c->O[2] + h;
+    const double X = c->O[0] + h, Y = c->O[1] + h, Z = c->O[2] + 0.5 * (c->Lz - 1) * c->R;
     const double w = a[8] * X + a[9] * Y + a[10] * Z + a[11];
     const double u = (a[0] * X + a[1] * Y + a[2] * Z + a[3]) / w;
     const double v = (a[4] * X + a[5] * Y + a[6] * Z + a[7]) / w;
@@ -384,6 +399,7 @@ static VolGeom vol_geom(const bp_ctx *c)
 {
     VolGeom g;
     g.L = c->L;
+    g.Lz = c->Lz;
     g.R = (float)c->R;
     g.Ox = (float)c->O[0];
     g.Oy = (float)c->O[1];
@@ -532,7 +548,7 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
         int tile[3] = {kBrickX, kBrickY, kBrickZ};
         if (!tma)
             fwd_tile(c->lanes_x, &tile[0], &tile[1], &tile[2]);
-        const long long nb = tile_count(c->L, tile[0], tile[1], tile[2]);
+        const long long nb = tile_count(c->L, c->Lz, tile[0], tile[1], tile[2]);
         {
             b.n = m;
             double rows[kMaxBatch][3][4];   // the same centred rows in float64
@@ -563,7 +579,7 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
                 }
                 masks = c->masks[s];
             } else if (!tma) {
-                c->work_host += (unsigned long long)m * c->L * c->L * c->L;
+                c->work_host += (unsigned long long)m * c->L * c->L * c->Lz;
             }
             CentreBatch cb;
             if (c->dtype == BP_F32 && c->block_centre) {
@@ -710,7 +726,7 @@ extern "C" bp_status bp_finalize(bp_ctx *c, float *vol_out, int on_device)
     if (vol_out == nullptr)
         return fail(c, BP_EINVAL, "bp_finalize: NULL output");
     CTX_CK(c, cudaSetDevice(c->device));
-    const size_t bytes = sizeof(float) * (size_t)c->L * c->L * c->L;
+    const size_t bytes = sizeof(float) * (size_t)c->L * c->L * c->Lz;
     CTX_CK(c, cudaMemcpyAsync(vol_out, c->vol, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                               c->stream));
     CTX_CK(c, cudaStreamSynchronize(c->stream));
@@ -738,7 +754,7 @@ extern "C" bp_status bp_set_state(bp_ctx *c, const float *vol_in, int on_device,
     if (vol_in == nullptr || n_added < 0)
         return fail(c, BP_EINVAL, "bp_set_state: NULL volume or negative counter");
     CTX_CK(c, cudaSetDevice(c->device));
-    const size_t bytes = sizeof(float) * (size_t)c->L * c->L * c->L;
+    const size_t bytes = sizeof(float) * (size_t)c->L * c->L * c->Lz;
     CTX_CK(c, cudaMemcpyAsync(c->vol, vol_in, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                               c->stream));
     CTX_CK(c, cudaStreamSynchronize(c->stream));
@@ -762,7 +778,7 @@ extern "C" bp_status bp_adjoint(bp_ctx *c, const float *vol, int vol_on_device, 
     if (st != BP_OK)
         return st;
     CTX_CK(c, cudaSetDevice(c->device));
-    const size_t nvox = (size_t)c->L * c->L * c->L;
+    const size_t nvox = (size_t)c->L * c->L * c->Lz;
     const size_t img_elems = (size_t)c->isx * c->isy;
     const float *dvol = vol;
     float *dvol_tmp = nullptr, *dout = images_out;
@@ -785,7 +801,7 @@ extern "C" bp_status bp_adjoint(bp_ctx *c, const float *vol, int vol_on_device, 
     // BP_OPT_BLOCK_CENTRE: its records come from the per-tile pre-pass, on
     // this stream, with the kernel's block as the tile.
     const bool blk = c->cull && c->block_centre;
-    const long long nb = tile_count(c->L, kAdjBlockX, kAdjBlockY, kAdjBlockZ);
+    const long long nb = tile_count(c->L, c->Lz, kAdjBlockX, kAdjBlockY, kAdjBlockZ);
     if (e == cudaSuccess && blk && nb > c->adj_blocks) {
         if (c->adj_centres)
             e = cudaFree(c->adj_centres);

@@ -103,7 +103,7 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
         }
         __syncthreads();
     }
-    if (y >= L || z >= L)
+    if (y >= L || z >= g.Lz)
         return;
 
     // Voxel coordinates: absolute, or with BLK offsets from the centre of the
@@ -113,7 +113,7 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * LZ;
     const float hx = 0.5f * (float)(x0 + min(x0 + TX, L) - 1);
     const float hy = 0.5f * (float)(y0 + min(y0 + TY, L) - 1);
-    const float hz = 0.5f * (float)(z0 + min(z0 + LZ, L) - 1);
+    const float hz = 0.5f * (float)(z0 + min(z0 + LZ, g.Lz) - 1);
     float X[VPL];
 #pragma unroll
     for (int k = 0; k < VPL; ++k)
@@ -196,9 +196,9 @@ void fwd_tile(int lanes_x, int *tx, int *ty, int *tz)
     *tz = 32 / (lx * ly);
 }
 
-long long tile_count(int L, int tx, int ty, int tz)
+long long tile_count(int L, int Lz, int tx, int ty, int tz)
 {
-    return (long long)((L + tx - 1) / tx) * ((L + ty - 1) / ty) * ((L + tz - 1) / tz);
+    return (long long)((L + tx - 1) / tx) * ((L + ty - 1) / ty) * ((Lz + tz - 1) / tz);
 }
 
 
@@ -207,7 +207,7 @@ static cudaError_t launch_lx(const FwdBatch &b, float *vol, const VolGeom &g, bo
                              const unsigned long long *masks, const float4 *centres, cudaStream_t s)
 {
     constexpr int TX = LX * VPL, TY = kWarpsY * LY, LZ = 32 / (LX * LY);
-    dim3 grid((g.L + TX - 1) / TX, (g.L + TY - 1) / TY, (g.L + LZ - 1) / LZ);
+    dim3 grid((g.L + TX - 1) / TX, (g.L + TY - 1) / TY, (g.Lz + LZ - 1) / LZ);
     if constexpr (KIND == kTexFloat) {
         if (centres) {
             bp_fwd_kernel<KIND, IEEE, LX, LY, VPL, true><<<grid, kThreads, 0, s>>>(b, vol, g, acc ? 1 : 0, masks,
@@ -388,7 +388,7 @@ block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__
     if (q < nblocks) {
         const int bx = (int)(q % nbx), by = (int)((q / nbx) % nby), bz = (int)(q / ((long long)nbx * nby));
         const int x0 = bx * tx, y0 = by * ty, z0 = bz * tz;
-        const int x1 = min(x0 + tx, g.L) - 1, y1 = min(y0 + ty, g.L) - 1, z1 = min(z0 + tz, g.L) - 1;
+        const int x1 = min(x0 + tx, g.L) - 1, y1 = min(y0 + ty, g.L) - 1, z1 = min(z0 + tz, g.Lz) - 1;
         unsigned long long m = 0;
         for (int i = 0; i < b.n; ++i) {
             if (masks && footprint_hits(b, i, g, isx, isy, x0, y0, z0, x1, y1, z1))
@@ -425,7 +425,7 @@ cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const
     if (!box)
         boxes = nullptr;
     const int nbx = (g.L + tx - 1) / tx, nby = (g.L + ty - 1) / ty;
-    const long long nblocks = tile_count(g.L, tx, ty, tz);
+    const long long nblocks = tile_count(g.L, g.Lz, tx, ty, tz);
     const unsigned grid = (unsigned)((nblocks + 255) / 256);
     if (centres && cb) {
         block_prepass_kernel<true><<<grid, 256, 0, s>>>(b, *cb, g, isx, isy, tx, ty, tz, nbx, nby, nblocks, masks,

@@ -50,8 +50,10 @@ struct AdjBatch {
 // its centring records).
 constexpr int kAdjBlockX = 32, kAdjBlockY = 32, kAdjBlockZ = 4;
 
+// Volume: L x L x Lz voxels (x fastest; Lz = L for a cube, Lz < L for a
+// z-slab of an L^3 grid), voxel size R, centre of voxel (0,0,0) at O.
 struct VolGeom {
-    int L;
+    int L, Lz;
     float R, Ox, Oy, Oz;
 };
 
@@ -103,9 +105,9 @@ cudaError_t launch_bp_fwd(const FwdBatch &b, float *vol, const VolGeom &g, int t
 // - centres (if not NULL, with cb): the tile's centring records;
 // - boxes (if not NULL, with box): the TMA path's box decisions (below);
 // - work (if not NULL): the kept updates are added to *work.
-// tile_count: tiles of an L^3 volume.
+// tile_count: tiles of an L x L x Lz volume.
 void fwd_tile(int lanes_x, int *tx, int *ty, int *tz);
-long long tile_count(int L, int tx, int ty, int tz);
+long long tile_count(int L, int Lz, int tx, int ty, int tz);
 // TMA-path box decision per (brick, projection), made by the pre-pass
 // (boxes, one int4 per pair at index projection * bricks + brick):
 //   (0, 0, 0, 0)            the footprint misses the detector: skip;

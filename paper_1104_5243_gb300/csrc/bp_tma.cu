@@ -335,7 +335,8 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
             }
         }
         if (computed) {
-            const int xe = min(bx0 + kBrickX, L) - 1, ye = min(by0 + kBrickY, L) - 1, ze = min(bz0 + kBrickZ, L) - 1;
+            const int xe = min(bx0 + kBrickX, L) - 1, ye = min(by0 + kBrickY, L) - 1;
+            const int ze = min(bz0 + kBrickZ, g.Lz) - 1;
             atomicAdd(work, computed * (unsigned long long)((xe - bx0 + 1) * (ye - by0 + 1) * (ze - bz0 + 1)));
         }
         if (*(volatile int *)&abort_flag) {
@@ -358,7 +359,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     const int x0 = bx0 + tx, y0 = by0 + warp, z0 = bz0 + tz;
     const float hx = 0.5f * (float)(bx0 + min(bx0 + kBrickX, L) - 1);
     const float hy = 0.5f * (float)(by0 + min(by0 + kBrickY, L) - 1);
-    const float hz = 0.5f * (float)(bz0 + min(bz0 + kBrickZ, L) - 1);
+    const float hz = 0.5f * (float)(bz0 + min(bz0 + kBrickZ, g.Lz) - 1);
     float X[4], Y[2], Z[2];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -367,7 +368,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const int y = min(y0 + 8 * k, L - 1), z = min(z0 + 4 * k, L - 1);
+        const int y = min(y0 + 8 * k, L - 1), z = min(z0 + 4 * k, g.Lz - 1);
         Y[k] = BLK ? g.R * ((float)y - hy) : fmaf(g.R, (float)y, g.Oy);
         Z[k] = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)z, g.Oz);
     }
@@ -421,7 +422,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int y = y0 + 8 * (q >> 1), z = z0 + 4 * (q & 1);
-        if (y >= L || z >= L)
+        if (y >= L || z >= g.Lz)
             continue;
         float *row = vol + ((size_t)z * L + y) * L;
 #pragma unroll
@@ -437,7 +438,7 @@ template <int KIND, bool IEEE, bool BLK>
 static cudaError_t launch_tma_blk(const TmaBatch &b, float *vol, const VolGeom &g, bool acc, int *err,
                                   unsigned long long *work, cudaStream_t s)
 {
-    dim3 grid((g.L + kBrickX - 1) / kBrickX, (g.L + kBrickY - 1) / kBrickY, (g.L + kBrickZ - 1) / kBrickZ);
+    dim3 grid((g.L + kBrickX - 1) / kBrickX, (g.L + kBrickY - 1) / kBrickY, (g.Lz + kBrickZ - 1) / kBrickZ);
     using T = typename Pairs<KIND>::T;
     const size_t smem = sizeof(T) * TmaStage<KIND>::kElems * TmaBox<KIND>::S;
     // the ring exceeds the 48 KB default for float32 pairs (set per call:

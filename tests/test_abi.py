@@ -88,3 +88,12 @@ def test_bounded_wait_selftest_validates_arguments_without_the_gpu(lib):
     assert lib.bp_selftest_bounded_wait(0, 0) == N.BP_EINVAL
     assert lib.bp_selftest_bounded_wait(1, (1 << 20) + 1) == N.BP_EINVAL
     assert "bp_selftest_bounded_wait" in N.bp_last_error(None)
+
+
+def test_create_slab_validates_the_slab_without_the_gpu(lib):
+    h = ctypes.c_void_p()
+    O = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    for (L, nz, z0) in [(8, 0, 0), (8, 9, 0), (8, 4, -1), (8, 4, 5), (0, 1, 0)]:
+        st = lib.bp_create_slab(ctypes.byref(h), L, nz, z0, 1.0, ctypes.cast(O, ctypes.c_void_p), 8, 8, 0, None)
+        assert st == N.BP_EINVAL, (L, nz, z0)
+        assert h.value is None
