@@ -82,24 +82,26 @@ def roofline_peak_gups(path: str, form: str, sm_mhz: float, sms: int, gather_per
     return bounds
 
 
-def algorithmic_bytes(L: int, n: int, isx: int, isy: int, form: str, path: str, computed_fraction: float) -> int:
+def algorithmic_bytes(L: int, n: int, isx: int, isy: int, form: str, path: str, computed_fraction: float,
+                       Lz: int | None = None) -> int:
     """Bytes one mid-step launch of the backprojection kernel must move: the
-    volume read and written once, each of the n projections read once (the
-    TMA path reads pair images: two pixels per element, row pitch padded to
+    L x L x Lz volume (Lz = L for the whole cube) read and written once, each
+    of the n projections read once (the TMA path reads pair images: two pixels per element, row pitch padded to
     16 B), and for the FP32 form the per-block centring records (3 x 16 B)
     of the (block, projection) pairs it computes (texture blocks of
     32 x 8 x 4 voxels, TMA bricks of 32 x 16 x 8)."""
     px = 4 if form == "f32" else 2
+    Lz = L if Lz is None else Lz
     if path == "tma":
         align = 2 if form == "f32" else 4
         pitch = -(-(isx + 1) // align) * align
-        total = 8 * L ** 3 + n * pitch * isy * 2 * px
+        total = 8 * L * L * Lz + n * pitch * isy * 2 * px
         tile = (32, 16, 8)
     else:
-        total = 8 * L ** 3 + n * isx * isy * px
+        total = 8 * L * L * Lz + n * isx * isy * px
         tile = (32, 8, 4)
     if form == "f32":
-        blocks = -(-L // tile[0]) * -(-L // tile[1]) * -(-L // tile[2])
+        blocks = -(-L // tile[0]) * -(-L // tile[1]) * -(-Lz // tile[2])
         total += int(48 * n * blocks * computed_fraction)
     return int(total)
 
@@ -200,9 +202,11 @@ def gpu_id_for_smi(torch, dev: int) -> str | None:
 
 
 # ---------------------------------------------------------------------------
-# Multi-rank bookkeeping (one process per GPU, independent reconstructions,
-# no data-path collective): the slowest rank's time decides, and the value is
-# the work of all ranks over that time.
+# Multi-rank bookkeeping (one process per GPU, no data-path collective): the
+# slowest rank's time decides, and the value is the work of all ranks over
+# that time.  By default every rank reconstructs its own volume (weak
+# scaling); with --split z the ranks share one volume, each the z-slab
+# slab_of_rank gives it, from the whole projection stack (strong scaling).
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
     if dist is None:
         return x
@@ -215,6 +219,23 @@ def max_over_ranks(x: float, dist=None, device="cpu") -> float:
 def whole_job_gups(updates_per_rank: int, steps: int, world: int, max_ms: float) -> float:
     """GUP/s of the whole job: every rank's updates over the slowest rank's time."""
     return updates_per_rank * steps * world / (max_ms / 1e3) / 1e9
+
+
+def slab_of_rank(L: int, world: int, rank: int, granule: int = 8) -> tuple[int, int]:
+    """(z0, nz) of this rank's slab when the z extent of an L^3 volume is
+    split over world ranks, as the paper splits the z loop between threads
+    (Sect. 6): contiguous slabs of whole granules (the z depth of one TMA
+    brick, so no rank computes a partial brick except at the top of the
+    volume), in rank order, sizes differing by at most one granule.  A rank
+    left without a granule gets nz = 0."""
+    if L < 1 or world < 1 or not 0 <= rank < world or granule < 1:
+        raise ValueError("slab_of_rank: need L >= 1, world >= 1, 0 <= rank < world, granule >= 1")
+    units = -(-L // granule)
+    q, r = divmod(units, world)
+    u0 = rank * q + min(rank, r)
+    u1 = u0 + q + (1 if rank < r else 0)
+    z0, z1 = min(L, u0 * granule), min(L, u1 * granule)
+    return z0, z1 - z0
 
 
 def cpu_baseline(L: int, n_sample: int):
@@ -290,6 +311,9 @@ def main():
     ap.add_argument("--path", default="auto", choices=["auto", "texture", "tma"],
                     help="data path of the backprojection (profiling runs; default: the library's choice)")
     ap.add_argument("--n-proj", type=int, default=496, help="projections per step (profiling runs)")
+    ap.add_argument("--split", default="replica", choices=["replica", "z"],
+                    help="replica: each rank reconstructs its own volume (weak scaling); z: the ranks "
+                         "share one volume, one z-slab each (strong scaling)")
     ap.add_argument("--cpu-proj", type=int, default=128, help="projections in the oracle sample")
     ap.add_argument("--ref-proj", type=int, default=48, help="projections per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -305,6 +329,8 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    if args.split == "z" and world > -(-args.L // 8):      # every rank sees the same sizes and stops here
+        ap.error(f"--split z: {world} ranks but only {-(-args.L // 8)} slabs of 8 slices")
 
     import numpy as np
     import torch
@@ -327,8 +353,10 @@ def main():
     A = api.carm_matrices(scan)                         # FP64 on the GPU
     stack_host = torch.from_numpy(synth.uniform_stack(scan.n, scan.isy, scan.isx)).pin_memory()
     stack = stack_host.cuda()
-    updates = args.L ** 3 * scan.n
-    out = torch.empty((args.L,) * 3, dtype=torch.float32, device="cuda")
+    z0, nz = (0, args.L) if args.split == "replica" else slab_of_rank(args.L, world, rank)
+    updates = args.L * args.L * nz * scan.n           # this rank's updates per step
+    job_updates = updates * world if args.split == "replica" else args.L ** 3 * scan.n
+    out = torch.empty((nz, args.L, args.L), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -348,7 +376,7 @@ def main():
     path_taken = {}
     clocks = None
     for form in args.forms.split(","):
-        bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=form)
+        bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=form, nz=nz, z0=z0)
         bp.set_option(N.BP_OPT_PATH, {"auto": 0, "texture": 1, "tma": 2}[args.path])
 
         def step():
@@ -375,7 +403,7 @@ def main():
         computed = bp.query(N.BP_QUERY_UPDATES_COMPUTED) - computed0
         path_taken[form] = bp.last_path
         bp.set_option(N.BP_OPT_TIMING, 0)
-        gups = whole_job_gups(updates, args.steps, world, ms)
+        gups = whole_job_gups(job_updates, args.steps, 1, ms)
         forms[form] = {"value": round(gups, 2), "ms_per_step": round(ms / args.steps, 3)}
         kernel[form] = {"launches": launches, "kernel_ms": kms,
                         "kernel_gups": updates * args.steps / (kms / 1e3) / 1e9 if kms > 0 else None,
@@ -389,8 +417,8 @@ def main():
     # out to pinned host memory, every step.
     e2e = None
     if not args.no_e2e:
-        vol_host = torch.empty((args.L,) * 3, dtype=torch.float32).pin_memory()
-        bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype="f32")
+        vol_host = torch.empty((nz, args.L, args.L), dtype=torch.float32).pin_memory()
+        bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype="f32", nz=nz, z0=z0)
 
         def step_e2e():
             bp.reset()
@@ -406,7 +434,7 @@ def main():
         torch.cuda.synchronize()
         wall = rank_max(time.perf_counter() - t0)
         bp.close()
-        e2e = {"value": round(whole_job_gups(updates, args.steps, world, wall * 1e3), 2), "unit": UNIT,
+        e2e = {"value": round(whole_job_gups(job_updates, args.steps, 1, wall * 1e3), 2), "unit": UNIT,
                "h2d_bytes_per_step": int(stack_host.numel() * 4),
                "d2h_bytes_per_step": int(vol_host.numel() * 4)}
 
@@ -462,7 +490,7 @@ def main():
     achieved = k["kernel_gups_computed"]
     head_path = path_taken.get(head, "texture")
     kname, ksrc = ("bp_tma_kernel", "bp_tma.cu") if head_path == "tma" else ("bp_fwd_kernel", "bp_fwd.cu")
-    traffic = ncu_traffic(ksrc, f"{kname}_{head}_{args.L}.md") if args.n_proj == 496 else None
+    traffic = ncu_traffic(ksrc, f"{kname}_{head}_{args.L}.md") if args.n_proj == 496 and nz == args.L else None
     basis = ("shared-memory bandwidth" if head_path == "tma" else "measured texture gather rate")
     roofline = {
         "bound": "alu", "unit": UNIT, "kernel": f"{kname} ({head} projections, {head_path} path)",
@@ -480,7 +508,7 @@ def main():
         "launches": k["launches"],
         "traffic": traffic,
         "algorithmic_bytes_per_launch": algorithmic_bytes(vol.L, min(scan.n, 64), scan.isx, scan.isy, head,
-                                                          head_path, k["computed_fraction"]),
+                                                          head_path, k["computed_fraction"], nz),
     }
     cpu = None
     if not args.no_cpu_baseline:
@@ -489,12 +517,15 @@ def main():
     line = {
         "metric": METRIC, "value": f32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": f32["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak" if args.split == "replica" else "strong", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
         "config": {"workload": f"FDK backprojection {args.L}^3 x {scan.n} x {scan.isx}x{scan.isy}, "
                                f"uniform [0,1) stack seed 20110426, {scan.scan_deg:.0f}-degree C-arm",
                    "L": args.L, "n_proj": scan.n, "detector": [scan.isx, scan.isy],
                    "l2": "inputs larger than L2 (2.38 GB projections + 0.54 GB volume per step)",
-                   "step": "reset + bp_add_projections(496, device-resident) + finalize"},
+                   "step": "reset + bp_add_projections(496, device-resident) + finalize",
+                   "parallelism": (f"replicas x{world}" if args.split == "replica"
+                                   else f"z-slabs x{world} (rank 0: z {z0}..{z0 + nz - 1})")},
         "forms": {kk: {**v, "kernel_gups": round(kernel[kk]["kernel_gups"], 2),
                        "kernel_gups_computed": round(kernel[kk]["kernel_gups_computed"], 2),
                        "frac_of_roofline": round(kernel[kk]["kernel_gups_computed"] / peaks[kk]["min"], 4),

@@ -71,3 +71,54 @@ def test_ncu_traffic_reads_the_committed_summary():
     current = hashlib.sha256(open(src, "rb").read()).hexdigest() in text
     t = bench.ncu_traffic("bp_tma.cu", "bp_tma_kernel_f32_512.md")
     assert (t is not None and t > 1e9) if current else t is None
+
+
+@pytest.mark.parametrize("L", [1, 7, 8, 64, 100, 512, 1024])
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
+def test_z_slabs_partition_the_volume(L, world):
+    """The ranks' z-slabs tile [0, L) in rank order without gaps or overlap,
+    start on multiples of the 8-slice granule, and differ in size by at most
+    one granule (Sect. 6's static split of the z loop)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    slabs = [bench.slab_of_rank(L, world, r) for r in range(world)]
+    z = 0
+    for z0, nz in slabs:
+        assert z0 == z and nz >= 0 and (nz == 0 or z0 % 8 == 0)
+        z += nz
+    assert z == L
+    full = [nz for z0, nz in slabs if z0 + nz < L]          # slabs below the top one
+    if full:
+        assert max(full) - min(full) <= 8
+    if world <= -(-L // 8):
+        assert all(nz > 0 for _, nz in slabs)
+
+
+def test_z_slab_split_rejects_bad_arguments():
+    sys.path.insert(0, ROOT)
+    import bench
+    for args in [(0, 1, 0), (8, 0, 0), (8, 2, 2), (8, 2, -1)]:
+        with pytest.raises(ValueError):
+            bench.slab_of_rank(*args)
+
+
+def _rank_main_z(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    z0, nz = bench.slab_of_rank(512, world, rank)
+    my_ms = [80.0, 90.0][rank]
+    mx = bench.max_over_ranks(my_ms, dist, "cpu")
+    dist.barrier()
+    # strong scaling: the job is one 512^3 volume, whatever the rank count
+    out[rank] = (z0, nz, mx, bench.whole_job_gups(512 ** 3 * 496, 5, 1, mx))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_share_one_volume_by_z_slabs():
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_rank_main_z, args=(world, port, out), nprocs=world, join=True)
+    assert (out[0][0], out[0][1]) == (0, 256) and (out[1][0], out[1][1]) == (256, 256)
+    assert out[0][2] == out[1][2] == 90.0
+    assert out[0][3] == pytest.approx(512 ** 3 * 496 * 5 / 0.090 / 1e9)
