@@ -101,13 +101,14 @@ bp_adjoint_kernel(const __grid_constant__ AdjBatch b, const float *__restrict__ 
 
 // Shared-memory accumulation.  Per projection, 8 lanes of warp 0 project
 // the corners of the block's voxel box and the block agrees on its footprint
-// on the detector (clipped to it, with a pixel of margin).  Then
+// (with a pixel of margin, not clipped to the detector, so that every corner
+// of every voxel falls inside it without a test).  Then
 //   * footprint off the detector: the projection is skipped (all of its
 //     terms would be dropped -- block culling, as in the forward kernel);
 //   * footprint of at most kAdjTile pixels: the block zeroes a tile of that
 //     size, scatters its 4 weighted corners per update into it, and adds the
-//     tile's nonzero pixels to the image with one global atomic each (a few
-//     hundred per block instead of 4 per update);
+//     tile's nonzero pixels on the detector to the image with one global
+//     atomic each (a few hundred per block instead of 4 per update);
 //   * larger footprint: global atomics per update, as in the direct kernel.
 // The tile accumulates in 32-bit fixed point with native integer
 // shared-memory atomics: float, and 64-bit integer, shared-memory atomics
@@ -235,14 +236,17 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
                 umax = fminf(fmaxf(umax, -1.0e6f), 1.0e6f);
                 vmin = fminf(fmaxf(vmin, -1.0e6f), 1.0e6f);
                 vmax = fminf(fmaxf(vmax, -1.0e6f), 1.0e6f);
-                // pixels touched: floor(u) .. floor(u) + 1 with u = u' + ku, one of margin
+                // pixels touched: floor(u) .. floor(u) + 1 with u = u' + ku, one of
+                // margin; the box is not clipped to the detector, so every
+                // corner of every voxel of the block lies inside it (the
+                // projection of the block is the hull of its corners'), and
+                // the flush drops the pixels outside the detector
                 const int x0 = (int)floorf(umin) + kc.x - 1, x1 = (int)floorf(umax) + kc.x + 2;
                 const int y0 = (int)floorf(vmin) + kc.y - 1, y1 = (int)floorf(vmax) + kc.y + 2;
-                const int cx0 = max(x0, 0), cx1 = min(x1, isx - 1), cy0 = max(y0, 0), cy1 = min(y1, isy - 1);
-                int4 p = make_int4(cx0, cy0, 0, 0);
-                if (cx0 <= cx1 && cy0 <= cy1) {
-                    const int W = cx1 - cx0 + 1, H = cy1 - cy0 + 1;
-                    p.z = W * H <= kAdjTile ? W : -1;
+                int4 p = make_int4(x0, y0, 0, 0);
+                if (x1 >= 0 && x0 <= isx - 1 && y1 >= 0 && y0 <= isy - 1) {
+                    const int W = x1 - x0 + 1, H = y1 - y0 + 1;   // at least 4 each
+                    p.z = (W <= kAdjTile && H <= kAdjTile && W * H <= kAdjTile) ? W : -1;
                     p.w = H;
                 }
                 // fixed-point scale 2^e with B * 2^e <= 2^(kAccBits - 2), B the
@@ -283,47 +287,73 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
             vw4.w = rec[2][i].x;
             kb = make_int2((int)rec[2][i].y - 1, (int)rec[2][i].z - 1);
         }
-        const float ulo = (float)(-1 - kb.x), uhi = (float)(isx - kb.x);
-        const float vlo = (float)(-1 - kb.y), vhi = (float)(isy - kb.y);
+        if (tiled) {
+            // Every corner lands in the tile (the box covers the block's
+            // footprint with a pixel of margin), so there is no per-corner
+            // test; the clamp keeps the four addresses inside the array
+            // whatever the rounding.  The fixed-point scale (a power of two)
+            // is folded into the weight: the terms equal the scaled ones of
+            // the global path exactly.
+            const int W = p.z;
+            const unsigned qmax = (unsigned)(W * p.w - W - 2);
+            const int du = kb.x - p.x, dv = kb.y - p.y;
 #pragma unroll
-        for (int ky = 0; ky < kAdjVPY; ++ky) {
-            const float bu = fmaf(vu.y, Y[ky], fmaf(vu.z, Z, vu.w));
-            const float bv = fmaf(vv.y, Y[ky], fmaf(vv.z, Z, vv.w));
-            const float bw = fmaf(vw4.y, Y[ky], fmaf(vw4.z, Z, vw4.w));
+            for (int ky = 0; ky < kAdjVPY; ++ky) {
+                const float bu = fmaf(vu.y, Y[ky], fmaf(vu.z, Z, vu.w));
+                const float bv = fmaf(vv.y, Y[ky], fmaf(vv.z, Z, vv.w));
+                const float bw = fmaf(vw4.y, Y[ky], fmaf(vw4.z, Z, vw4.w));
 #pragma unroll
-            for (int k = 0; k < kVoxPerLane; ++k) {
-                if (f[ky][k] == 0.f)
-                    continue;
-                const float uw = fmaf(vu.x, X[k], bu);
-                const float vw = fmaf(vv.x, X[k], bv);
-                const float w = fmaf(vw4.x, X[k], bw);
-                const float r = recip_adj<IEEE>(w);
-                const float u = uw * r, v = vw * r;
-                if (!(u > ulo && u < uhi && v > vlo && v < vhi))
-                    continue;
-                const float fu0 = floorf(u), fv0 = floorf(v);
-                const int iu = (int)fu0 + kb.x, iv = (int)fv0 + kb.y;
-                const float fu = u - fu0, fv = v - fv0;
-                const float s = f[ky][k] * (r * r);
-                const float sb = s * fv, st = s - sb;
-                const float w_tr = st * fu, w_tl = st - w_tr;
-                const float w_br = sb * fu, w_bl = sb - w_br;
-                const bool in_l = iu >= 0, in_r = iu + 1 < isx, in_t = iv >= 0, in_b = iv + 1 < isy;
-                if (tiled) {
-                    // index in the tile; the footprint box covers every in-detector
-                    // corner, the unsigned clamp only guards the array
-                    const int q0 = (iv - p.y) * p.z + (iu - p.x);
-                    auto at = [&](int d) { return &tile[min((unsigned)(q0 + d), (unsigned)(kAdjTile - 1))]; };
-                    auto add = [&](int d, float t) { atomicAdd(at(d), __float2int_rn(t * sc.x)); };
-                    if (in_t) {
-                        if (in_l) add(0, w_tl);
-                        if (in_r) add(1, w_tr);
-                    }
-                    if (in_b) {
-                        if (in_l) add(p.z, w_bl);
-                        if (in_r) add(p.z + 1, w_br);
-                    }
-                } else {
+                for (int k = 0; k < kVoxPerLane; ++k) {
+                    if (f[ky][k] == 0.f)
+                        continue;
+                    const float uw = fmaf(vu.x, X[k], bu);
+                    const float vw = fmaf(vv.x, X[k], bv);
+                    const float w = fmaf(vw4.x, X[k], bw);
+                    const float r = recip_adj<IEEE>(w);
+                    const float u = uw * r, v = vw * r;
+                    const float fu0 = floorf(u), fv0 = floorf(v);
+                    const unsigned q0 =
+                        min((unsigned)(((int)fv0 + dv) * W + ((int)fu0 + du)), qmax);
+                    const float fu = u - fu0, fv = v - fv0;
+                    const float s = f[ky][k] * ((r * sc.x) * r);
+                    const float sb = s * fv, st = s - sb;
+                    const float w_tr = st * fu, w_tl = st - w_tr;
+                    const float w_br = sb * fu, w_bl = sb - w_br;
+                    atomicAdd(&tile[q0], __float2int_rn(w_tl));
+                    atomicAdd(&tile[q0 + 1], __float2int_rn(w_tr));
+                    atomicAdd(&tile[q0 + W], __float2int_rn(w_bl));
+                    atomicAdd(&tile[q0 + W + 1], __float2int_rn(w_br));
+                }
+            }
+        } else {
+            // footprint larger than the tile: global atomics, pixels outside
+            // the detector dropped
+            const float ulo = (float)(-1 - kb.x), uhi = (float)(isx - kb.x);
+            const float vlo = (float)(-1 - kb.y), vhi = (float)(isy - kb.y);
+#pragma unroll
+            for (int ky = 0; ky < kAdjVPY; ++ky) {
+                const float bu = fmaf(vu.y, Y[ky], fmaf(vu.z, Z, vu.w));
+                const float bv = fmaf(vv.y, Y[ky], fmaf(vv.z, Z, vv.w));
+                const float bw = fmaf(vw4.y, Y[ky], fmaf(vw4.z, Z, vw4.w));
+#pragma unroll
+                for (int k = 0; k < kVoxPerLane; ++k) {
+                    if (f[ky][k] == 0.f)
+                        continue;
+                    const float uw = fmaf(vu.x, X[k], bu);
+                    const float vw = fmaf(vv.x, X[k], bv);
+                    const float w = fmaf(vw4.x, X[k], bw);
+                    const float r = recip_adj<IEEE>(w);
+                    const float u = uw * r, v = vw * r;
+                    if (!(u > ulo && u < uhi && v > vlo && v < vhi))
+                        continue;
+                    const float fu0 = floorf(u), fv0 = floorf(v);
+                    const int iu = (int)fu0 + kb.x, iv = (int)fv0 + kb.y;
+                    const float fu = u - fu0, fv = v - fv0;
+                    const float s = f[ky][k] * (r * r);
+                    const float sb = s * fv, st = s - sb;
+                    const float w_tr = st * fu, w_tl = st - w_tr;
+                    const float w_br = sb * fu, w_bl = sb - w_br;
+                    const bool in_l = iu >= 0, in_r = iu + 1 < isx, in_t = iv >= 0, in_b = iv + 1 < isy;
                     const long long base = (long long)iv * isx + iu;
                     if (in_t) {
                         if (in_l) atomicAdd(img + base, w_tl);
@@ -338,11 +368,14 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
         }
         if (tiled) {
             __syncthreads();
-            // one warp per tile row, lanes along the row (no index division)
-            for (int row = threadIdx.x >> 5; row < p.w; row += kThreads / 32) {
+            // one warp per tile row, lanes along the row (no index division);
+            // only the part of the tile on the detector
+            const int c0 = max(0, -p.x), c1 = min(p.z, isx - p.x);
+            const int r0 = max(0, -p.y), r1 = min(p.w, isy - p.y);
+            for (int row = r0 + (threadIdx.x >> 5); row < r1; row += kThreads / 32) {
                 float *dst = img + (long long)(p.y + row) * isx + p.x;
                 const AdjAcc *src = tile + row * p.z;
-                for (int col = lane; col < p.z; col += 32) {
+                for (int col = c0 + lane; col < c1; col += 32) {
                     const AdjAcc v = src[col];
                     if (v != 0)
                         atomicAdd(dst + col, (float)v * sc.y);
