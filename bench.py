@@ -60,6 +60,23 @@ INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", 
                     ("tma", "bf16"): 34.6}
 MUFU_PER_SM_CLK = 16.0
 SMEM_BYTES_PER_SM_CLK = 128.0
+# Adjoint tile kernel (bp_adjoint_smem_kernel), 256^3 -> 248 x 624x480:
+#   issue: ncu's instructions per update (profiles/bp_adjoint_smem_kernel_256.md);
+#   smem_atomics: four shared-memory atomics per update, each warp instruction
+#     taking the wavefronts ncu measures (bank conflicts included: 32
+#     scattered addresses over 32 banks), one wavefront per SM per clock.
+ADJ_INSTR_PER_UPDATE = 50.0
+ADJ_ATOMIC_WAVEFRONTS = 3.7
+
+
+def adjoint_roofline_gups(sm_mhz: float, sms: int) -> dict:
+    f = sm_mhz * 1e6
+    bounds = {"issue": sms * ISSUE_PER_SM_CLK / ADJ_INSTR_PER_UPDATE * f / 1e9,
+              "smem_atomics": sms / (4 * ADJ_ATOMIC_WAVEFRONTS / 32) * f / 1e9}
+    bounds["min"] = min(bounds.values())
+    return bounds
+
+
 def tma_smem_bytes_per_update(form: str) -> float:
     pair, bu = (8, 114) if form == "f32" else (4, 100)
     return 2.0 * pair + bu * 36 * pair / (32 * 16 * 8)
@@ -462,8 +479,17 @@ def main():
         torch.cuda.synchronize()
         ams = t0.elapsed_time(t1) / args.steps
         bp.close()
+        agups = 256 ** 3 * half.n / (ams / 1e3) / 1e9
+        abounds = adjoint_roofline_gups((clocks or {}).get("sm_mhz") or 2070.0, sms)
         extra["adjoint"] = {"workload": "B^T 256^3 -> 248 x 624x480", "ms_per_call": round(ams, 3),
-                            "gups": round(256 ** 3 * half.n / (ams / 1e3) / 1e9, 2)}
+                            "gups": round(agups, 2),
+                            "roofline": {"bound": "smem_atomics" if abounds["min"] == abounds["smem_atomics"]
+                                         else "issue", "achieved": round(agups, 2),
+                                         "peak": round(abounds["min"], 1), "unit": UNIT,
+                                         "frac": round(agups / abounds["min"], 4),
+                                         "bounds_gups": {k: round(v, 1) for k, v in abounds.items()},
+                                         "note": "achieved is per call (4 launches, the output zeroing "
+                                                 "and the centring pre-pass included)"}}
         from paper_1104_5243_gb300 import learned as lm
         torch.manual_seed(0)
         lm.train(steps=args.warmup, batch=8)

@@ -122,3 +122,15 @@ def test_two_gloo_ranks_share_one_volume_by_z_slabs():
     assert (out[0][0], out[0][1]) == (0, 256) and (out[1][0], out[1][1]) == (256, 256)
     assert out[0][2] == out[1][2] == 90.0
     assert out[0][3] == pytest.approx(512 ** 3 * 496 * 5 / 0.090 / 1e9)
+
+
+def test_adjoint_roofline_bounds():
+    """The adjoint's bounds: issue at the measured instructions per update,
+    shared-memory atomics at four per update with the measured wavefronts per
+    atomic instruction, one wavefront per SM per clock."""
+    sys.path.insert(0, ROOT)
+    import bench
+    b = bench.adjoint_roofline_gups(2000.0, 100)
+    assert b["issue"] == pytest.approx(100 * 128 / bench.ADJ_INSTR_PER_UPDATE * 2.0)
+    assert b["smem_atomics"] == pytest.approx(100 * 2.0 * 32 / (4 * bench.ADJ_ATOMIC_WAVEFRONTS))
+    assert b["min"] == min(b["issue"], b["smem_atomics"])
