@@ -179,6 +179,22 @@ bp_status bp_add_projections(bp_ctx *ctx, const float *images, int images_on_dev
  * accumulating onto the same volume until bp_reset. */
 bp_status bp_finalize(bp_ctx *ctx, float *vol_out, int on_device);
 
+/* bp_add_projections followed by bp_finalize, in one call (Sect. 3.1: the
+ * images of a scan in, the finished volume out):
+ *   images, images_on_device, A, n: as bp_add_projections;
+ *   vol_out: the volume's L x L x Lz float32 destination, host
+ *            (out_on_device = 0) or device, owned by the caller.
+ * The result equals bp_add_projections + bp_finalize bit for bit, and the
+ * context keeps the volume as after them.  On the TMA path the last batch's
+ * launch also stores every voxel's final value into vol_out directly: device
+ * memory, or page-locked host memory (cudaHostAlloc, cudaHostRegister),
+ * through its device mapping, so the read-back overlaps that launch instead
+ * of following it.  Other host memory is copied after the launch.  The call
+ * synchronises.  n = 0 is bp_finalize.  Errors as bp_add_projections and
+ * bp_finalize (BP_EINVAL for a NULL context or output). */
+bp_status bp_add_projections_finalize(bp_ctx *ctx, const float *images, int images_on_device,
+                                      const double *A, int n, float *vol_out, int out_on_device);
+
 /* Checkpoint: copy the partial volume and the number of projections added so
  * far (synchronous).  vol_out may be NULL to read only the counter. */
 bp_status bp_get_state(bp_ctx *ctx, float *vol_out, int on_device, long long *n_added);

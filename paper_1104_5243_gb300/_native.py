@@ -26,6 +26,7 @@ SIGNATURES = {
     "bp_reset": (_i, [_vp]),
     "bp_add_projections": (_i, [_vp, _vp, _i, _vp, _i]),
     "bp_finalize": (_i, [_vp, _vp, _i]),
+    "bp_add_projections_finalize": (_i, [_vp, _vp, _i, _vp, _i, _vp, _i]),
     "bp_get_state": (_i, [_vp, _vp, _i, ctypes.POINTER(_ll)]),
     "bp_set_state": (_i, [_vp, _vp, _i, _ll]),
     "bp_adjoint": (_i, [_vp, _vp, _i, _vp, _i, _vp, _i]),
@@ -120,6 +121,11 @@ def bp_add_projections(ctx, images_ptr, images_on_device, A_ptr, n):
 
 def bp_finalize(ctx, vol_ptr, on_device):
     check(lib().bp_finalize(ctx, vol_ptr, int(on_device)), ctx)
+
+
+def bp_add_projections_finalize(ctx, images_ptr, images_on_device, A_ptr, n, vol_ptr, out_on_device):
+    check(lib().bp_add_projections_finalize(ctx, images_ptr, int(images_on_device), A_ptr, int(n), vol_ptr,
+                                            int(out_on_device)), ctx)
 
 
 def bp_get_state(ctx, vol_ptr, on_device):

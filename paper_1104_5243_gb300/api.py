@@ -139,6 +139,23 @@ class Backprojector:
         self._keep = None
         return out
 
+    def add_projections_finalize(self, images: torch.Tensor, A, out: torch.Tensor | None = None) -> torch.Tensor:
+        """add_projections then finalize in one call: the finished (nz, L, L)
+        volume in `out` (CUDA or host tensor; a pinned host tensor receives
+        it from the last kernel directly), bit-identical to the two calls."""
+        images = _f32(images, "images")
+        A = _matrices(A)
+        n = A.shape[0]
+        if tuple(images.shape) != (n, self.isy, self.isx):
+            raise ValueError(f"images must have shape {(n, self.isy, self.isx)}, got {tuple(images.shape)}")
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        out = self._volume(out, "out")
+        N.bp_add_projections_finalize(self._ctx, _ptr(images), images.is_cuda, ctypes.c_void_p(A.ctypes.data), n,
+                                      _ptr(out), out.is_cuda)
+        self._keep = None
+        return out
+
     def get_state(self):
         vol = torch.empty(self.shape, dtype=torch.float32, device=self.device)
         n = N.bp_get_state(self._ctx, _ptr(vol), 1)

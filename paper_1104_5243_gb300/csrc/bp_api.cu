@@ -463,8 +463,10 @@ static bp_status record_start(bp_ctx *c, cudaEvent_t *stop)
     return BP_OK;
 }
 
-extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int images_on_device,
-                                        const double *A, int n)
+// bp_add_projections; with final_out (device-addressable, or NULL) the last
+// batch's TMA launch also stores the finished volume there.
+static bp_status add_projections(bp_ctx *c, const float *images, int images_on_device, const double *A, int n,
+                                 float *final_out)
 {
     if (c == nullptr)
         return fail(nullptr, BP_EINVAL, "bp_add_projections: NULL context");
@@ -640,6 +642,7 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
             tb.centres = centres;
             tb.boxes = c->boxes[s];
             tb.bricks = nb;
+            tb.final_out = c0 + m == n ? final_out : nullptr;
             CTX_CK(c, launch_bp_tma(tb, c->vol, g, pair_kind(c), !c->vol_zero, c->ieee_rcp, c->err_dev, c->work_dev,
                                     c->stream));
         } else {
@@ -654,6 +657,12 @@ extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int imag
     }
     c->n_added += n;
     return BP_OK;
+}
+
+extern "C" bp_status bp_add_projections(bp_ctx *c, const float *images, int images_on_device,
+                                        const double *A, int n)
+{
+    return add_projections(c, images, images_on_device, A, n, nullptr);
 }
 
 // Turn the device-side error flag (a bounded wait that gave up) into a
@@ -731,6 +740,40 @@ extern "C" bp_status bp_finalize(bp_ctx *c, float *vol_out, int on_device)
                               c->stream));
     CTX_CK(c, cudaStreamSynchronize(c->stream));
     return check_device_error(c, "bp_finalize");
+}
+
+extern "C" bp_status bp_add_projections_finalize(bp_ctx *c, const float *images, int images_on_device,
+                                                 const double *A, int n, float *vol_out, int out_on_device)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_add_projections_finalize: NULL context");
+    if (vol_out == nullptr)
+        return fail(c, BP_EINVAL, "bp_add_projections_finalize: NULL output");
+    CTX_CK(c, cudaSetDevice(c->device));
+    // the destination as the kernel can address it: device memory as it is,
+    // page-locked host memory through its mapping; other host memory (no
+    // mapping) is copied after the last launch as bp_finalize does
+    float *direct = nullptr;
+    if (n > 0 && c->path != 1) {
+        if (out_on_device) {
+            direct = vol_out;
+        } else {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, vol_out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                at.devicePointer != nullptr)
+                direct = static_cast<float *>(at.devicePointer);
+            else
+                (void)cudaGetLastError();   // not a CUDA allocation: not an error here
+        }
+    }
+    bp_status st = add_projections(c, images, images_on_device, A, n, direct);
+    if (st != BP_OK)
+        return st;
+    if (direct != nullptr) {
+        CTX_CK(c, cudaStreamSynchronize(c->stream));
+        return check_device_error(c, "bp_add_projections_finalize");
+    }
+    return bp_finalize(c, vol_out, out_on_device);
 }
 
 extern "C" bp_status bp_get_state(bp_ctx *c, float *vol_out, int on_device, long long *n_added)

@@ -167,6 +167,9 @@ struct TmaBatch {
     const float4 *centres;             // per-brick centring records (NULL: per projection)
     const int4 *boxes;                 // per-(brick, projection) box decisions (pre-pass)
     long long bricks;                  // bricks of the volume (record plane stride)
+    float *final_out;                  // NULL, or a second destination of the updated volume
+                                       // (device-addressable, same layout): the finished
+                                       // volume written by the last batch's launch
     int n, isx, isy, pitch;            // pitch: pair elements per row
 };
 

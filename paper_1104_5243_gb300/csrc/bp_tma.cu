@@ -419,17 +419,26 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
 
     if (!ok)
         return;
+    // the volume's read-modify-write; with final_out the same values also go
+    // to the caller's destination (mapped host memory: the read-back of the
+    // finished volume then overlaps this launch instead of following it)
+    float *const fin = b.final_out;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int y = y0 + 8 * (q >> 1), z = z0 + 4 * (q & 1);
         if (y >= L || z >= g.Lz)
             continue;
-        float *row = vol + ((size_t)z * L + y) * L;
+        const size_t r0 = ((size_t)z * L + y) * L;
+        float *row = vol + r0;
 #pragma unroll
         for (int kx = 0; kx < 4; ++kx) {
             const int x = x0 + 8 * kx;
-            if (x < L)
-                row[x] = (accumulate ? row[x] : 0.f) + acc[q * 4 + kx];
+            if (x < L) {
+                const float v = (accumulate ? row[x] : 0.f) + acc[q * 4 + kx];
+                row[x] = v;
+                if (fin)
+                    fin[r0 + x] = v;
+            }
         }
     }
 }
