@@ -123,9 +123,11 @@ def algorithmic_bytes(L: int, n: int, isx: int, isy: int, form: str, path: str, 
     return int(total)
 
 
-def ncu_traffic(kernel_file: str, profile: str):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    summary is missing or the kernel source changed since it was captured."""
+def ncu_fields(kernel_file: str, profile: str, names) -> dict | None:
+    """Numbers from a committed ncu summary (its "- name: value" list items),
+    or None when the summary is missing, lacks one of them, or the kernel
+    source changed since it was captured (the summary records the source's
+    sha256)."""
     import hashlib
     try:
         text = open(os.path.join(ROOT, "profiles", profile)).read()
@@ -134,16 +136,28 @@ def ncu_traffic(kernel_file: str, profile: str):
         return None
     fields = {}
     for ln in text.splitlines():
-        item = ln.strip().lstrip("-* ").strip()   # "- name: value" list items
-        if ":" in item and item.startswith(("traffic_bytes_per_launch", "source_sha256")):
+        item = ln.strip().lstrip("-* ").strip()
+        if ":" in item and item.startswith(tuple(names) + ("source_sha256",)):
             k, v = item.split(":", 1)
             fields[k.strip("` ")] = v.strip().strip("`")
     if fields.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
     try:
-        return float(fields["traffic_bytes_per_launch"])
+        return {k: float(fields[k]) for k in names}
     except (KeyError, ValueError):
         return None
+
+
+def ncu_traffic(kernel_file: str, profile: str):
+    """DRAM bytes per launch from a committed ncu summary (None as ncu_fields)."""
+    f = ncu_fields(kernel_file, profile, ["traffic_bytes_per_launch"])
+    return None if f is None else f["traffic_bytes_per_launch"]
+
+
+# Utilisation of the FP32 (FMA) pipe, of shared memory and of DRAM, and the
+# issue rate, each in % of its peak, from the committed full ncu capture of
+# the dominant kernel on the 512^3 x 64 case.
+NCU_FRACTIONS = ["fma_pipe_pct", "smem_wavefronts_pct", "dram_pct", "issue_active_pct"]
 
 
 # ---------------------------------------------------------------------------
@@ -519,6 +533,7 @@ def main():
     head_path = path_taken.get(head, "texture")
     kname, ksrc = ("bp_tma_kernel", "bp_tma.cu") if head_path == "tma" else ("bp_fwd_kernel", "bp_fwd.cu")
     traffic = ncu_traffic(ksrc, f"{kname}_{head}_{args.L}.md") if args.n_proj == 496 and nz == args.L else None
+    ncu_pct = ncu_fields(ksrc, f"{kname}_{head}_{args.L}x64.md", NCU_FRACTIONS)
     basis = ("shared-memory bandwidth" if head_path == "tma" else "measured texture gather rate")
     roofline = {
         "bound": "alu", "unit": UNIT, "kernel": f"{kname} ({head} projections, {head_path} path)",
@@ -535,6 +550,8 @@ def main():
         "avg_launch_ms": round(k["kernel_ms"] / max(k["launches"], 1), 4),
         "launches": k["launches"],
         "traffic": traffic,
+        "ncu_pct_of_peak": (dict(ncu_pct, profile=f"profiles/{kname}_{head}_{args.L}x64.md")
+                            if ncu_pct else None),
         "algorithmic_bytes_per_launch": algorithmic_bytes(vol.L, min(scan.n, 64), scan.isx, scan.isy, head,
                                                           head_path, k["computed_fraction"], nz),
     }

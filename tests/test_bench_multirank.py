@@ -134,3 +134,22 @@ def test_adjoint_roofline_bounds():
     assert b["issue"] == pytest.approx(100 * 128 / bench.ADJ_INSTR_PER_UPDATE * 2.0)
     assert b["smem_atomics"] == pytest.approx(100 * 2.0 * 32 / (4 * bench.ADJ_ATOMIC_WAVEFRONTS))
     assert b["min"] == min(b["issue"], b["smem_atomics"])
+
+
+def test_ncu_fields_need_every_name_and_the_current_source(tmp_path, monkeypatch):
+    """A summary's numbers count only with every requested name present and
+    the recorded sha256 of the kernel source equal to the current one."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    root = tmp_path
+    (root / "profiles").mkdir()
+    (root / "paper_1104_5243_gb300" / "csrc").mkdir(parents=True)
+    (root / "paper_1104_5243_gb300" / "csrc" / "k.cu").write_bytes(b"kernel source")
+    sha = hashlib.sha256(b"kernel source").hexdigest()
+    (root / "profiles" / "p.md").write_text(f"text\n\n- fma_pipe_pct: 46.3\n- dram_pct: 6.7\n- source_sha256: {sha}\n")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.ncu_fields("k.cu", "p.md", ["fma_pipe_pct", "dram_pct"]) == {"fma_pipe_pct": 46.3, "dram_pct": 6.7}
+    assert bench.ncu_fields("k.cu", "p.md", ["fma_pipe_pct", "smem_wavefronts_pct"]) is None
+    (root / "paper_1104_5243_gb300" / "csrc" / "k.cu").write_bytes(b"changed")
+    assert bench.ncu_fields("k.cu", "p.md", ["fma_pipe_pct"]) is None
