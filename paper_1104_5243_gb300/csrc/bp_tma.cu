@@ -307,7 +307,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
         if (lane != 0)
             return;
         int issued = 0;            // stages whose tile may still be in flight
-        int last_use[S] = {};      // use index of each stage's last tile
+        unsigned last_par = 0;     // bit q: phase parity of stage q's last tile
         unsigned long long computed = 0;
         int k = 0;                 // projections computed so far
         for (int i = 0; i < b.n; ++i) {
@@ -328,7 +328,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                 mbar_expect_tx(&full[st], (uint32_t)(kBufElems * sizeof(T)));
                 tma_load_2d(buf[st], &b.map[i], bi.z * kPairWords<KIND>, bi.w, &full[st]);
                 issued |= 1 << st;
-                last_use[st] = use;
+                last_par = (last_par & ~(1u << st)) | ((unsigned)(use & 1) << st);
             } else {
                 mbar_arrive(&full[st]);
                 issued &= ~(1 << st);
@@ -343,7 +343,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
             // let copies still in flight land before the block's memory goes away
             for (int q = 0; q < S; ++q)
                 if (issued & (1 << q))
-                    mbar_wait_bounded(&full[q], last_use[q] & 1);
+                    mbar_wait_bounded(&full[q], (last_par >> q) & 1u);
         }
         return;
     }
