@@ -269,6 +269,20 @@ def slab_of_rank(L: int, world: int, rank: int, granule: int = 8) -> tuple[int, 
     return z0, z1 - z0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(L: int, n_sample: int):
     """The FP64 oracle (as it stands) on a bounded sample of the workload: the
     full L^3 volume backprojected from the first n_sample projections, with
@@ -287,6 +301,7 @@ def cpu_baseline(L: int, n_sample: int):
     dt = time.perf_counter() - t0
     gups = L ** 3 * n_sample / dt / 1e9
     return {"value": round(gups, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "cpu_model": cpu_model(), "affinity_cpus": len(os.sched_getaffinity(0)),
             "sample": f"{L}^3 volume x first {n_sample} of 496 projections (1248x960), FP64, "
                       f"{dt:.1f} s", "seconds": round(dt, 2)}
 
@@ -324,7 +339,7 @@ def run_reference(args, rank: int):
                                "20110426, 200-degree C-arm (bounded sample per step)",
                    "L": args.L, "n_proj": 496, "detector": [1248, 960]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[0]["cores"], "kind": "oracle",
-                         "sample": samples[0]["sample"]},
+                         "sample": samples[0]["sample"], "cpu_model": samples[0]["cpu_model"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -345,7 +360,7 @@ def main():
     ap.add_argument("--split", default="replica", choices=["replica", "z"],
                     help="replica: each rank reconstructs its own volume (weak scaling); z: the ranks "
                          "share one volume, one z-slab each (strong scaling)")
-    ap.add_argument("--cpu-proj", type=int, default=128, help="projections in the oracle sample")
+    ap.add_argument("--cpu-proj", type=int, default=160, help="projections in the oracle sample")
     ap.add_argument("--ref-proj", type=int, default=48, help="projections per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
