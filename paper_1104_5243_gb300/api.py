@@ -197,8 +197,9 @@ def backproject_slabs(L: int, R: float, O, images: torch.Tensor, A, slab: int, d
     for z0 in range(0, L, slab):
         nz = min(slab, L - z0)
         with Backprojector(L, R, O, isx, isy, dtype=dtype, nz=nz, z0=z0) as bp:
-            bp.add_projections(images, A)
-            bp.finalize(out[z0:z0 + nz])
+            # out[z0 : z0 + nz] is contiguous: with a pinned `out` the slab's
+            # last launch stores it there directly
+            bp.add_projections_finalize(images, A, out[z0:z0 + nz])
     return out
 
 
