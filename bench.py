@@ -269,6 +269,39 @@ def slab_of_rank(L: int, world: int, rank: int, granule: int = 8) -> tuple[int, 
     return z0, z1 - z0
 
 
+def reciprocal_modes(bp, step, out, stream, args, updates: int, gups_fast: float) -> dict:
+    """The paper's reciprocal comparison (Sect. 7.2): the same float32 step
+    with the IEEE reciprocal (BP_OPT_IEEE_RCP 1) against the approximate one
+    (the default), GUP/s of each and the PSNR of the approximate volume
+    against the IEEE one (M = max - min of the IEEE volume).  Runs after the
+    timed region."""
+    import math
+
+    import torch
+    from paper_1104_5243_gb300 import _native as N
+    step()
+    fast = out.clone()
+    bp.set_option(N.BP_OPT_IEEE_RCP, 1)
+    for _ in range(args.warmup):
+        step()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    ieee = out.clone()
+    bp.set_option(N.BP_OPT_IEEE_RCP, 0)
+    span = float(ieee.max() - ieee.min())
+    mse = float(((fast.double() - ieee.double()) ** 2).mean())
+    psnr = 10.0 * math.log10(span * span / mse) if mse > 0 else float("inf")
+    return {"approx_gups": round(gups_fast, 2), "ieee_gups": round(updates / (ms / 1e3) / 1e9, 2),
+            "psnr_approx_vs_ieee_db": round(psnr, 1),
+            "note": "f32, same workload and path; uniform [0,1) stack"}
+
+
 def cpu_model() -> str:
     """The host CPU's model name (lscpu), else the machine type."""
     import platform
@@ -421,6 +454,7 @@ def main():
     kernel = {}
     path_taken = {}
     clocks = None
+    rcp_modes = None
     for form in args.forms.split(","):
         bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=form, nz=nz, z0=z0)
         bp.set_option(N.BP_OPT_PATH, {"auto": 0, "texture": 1, "tma": 2}[args.path])
@@ -457,6 +491,9 @@ def main():
                         "kernel_gups_computed": computed / (kms / 1e3) / 1e9 if kms > 0 else None}
         if form == "f32":
             clocks = cs.summary()
+            if not args.no_extra:
+                rcp_modes = reciprocal_modes(bp, step, out, stream, args, updates,
+                                             updates * args.steps / (ms / 1e3) / 1e9)
         bp.close()
 
     # End to end through the public API: pinned host projections in, the
@@ -604,6 +641,7 @@ def main():
         "gpu_launches": sum(v["launches"] * 3 for kk, v in kernel.items()),
         "cpu_baseline": cpu,
         "paths": {kk: path_taken.get(kk) for kk in forms},
+        "reciprocal_modes": rcp_modes,
         **extra,
     }
     print(json.dumps(line), flush=True)
