@@ -637,8 +637,10 @@ def main():
         "e2e": e2e,
         # per batch of 64 projections: the copy/conversion kernel into the
         # projection arrays, the block pre-pass (culling masks; centring
-        # records for FP32) and the backprojection kernel
-        "gpu_launches": sum(v["launches"] * 3 for kk, v in kernel.items()),
+        # records for FP32) and the backprojection kernel; `value`'s timed
+        # region is the head form's
+        "gpu_launches": kernel[head]["launches"] * 3,
+        "gpu_launches_by_form": {kk: v["launches"] * 3 for kk, v in kernel.items()},
         "cpu_baseline": cpu,
         "paths": {kk: path_taken.get(kk) for kk in forms},
         "reciprocal_modes": rcp_modes,
