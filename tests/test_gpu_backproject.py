@@ -165,8 +165,8 @@ def test_gpu_matrices_match_oracle():
                                          (1024, "bf16", BF16_TOL)])
 def test_full_size_sampled_voxels(L, dtype, tol):
     """512^3 and 1024^3 x 496 x 1248x960, uniform timing stack, in the launch
-    configuration the benchmark times (batches of 64, device input, default
-    path: TMA for f32, texture for 16-bit); the oracle evaluates 4096
+    configuration the benchmark times (batches of 64, device input, the
+    automatic path: TMA for every storage type); the oracle evaluates 4096
     sampled voxels one by one."""
     api = native()
     scan, vol = synth.SCANS["full"], synth.Volume(L)
@@ -184,6 +184,35 @@ def test_full_size_sampled_voxels(L, dtype, tol):
           f"(max |ref| {np.abs(ref).max():.3e})")
     assert err <= tol
     bp.close()
+
+
+@pytest.mark.parametrize("L,dtype,tol", [(2048, "f32", FP32_TOL), (2048, "f16", FP16_TOL),
+                                         (500, "f32", FP32_TOL), (500, "bf16", BF16_TOL)])
+def test_largest_and_ragged_volumes_sampled(L, dtype, tol):
+    """The largest volume kept resident (2048^3, 32 GiB, 4.2e9 voxels: 64-bit
+    volume and record indexing) and a volume that is no multiple of the
+    32 x 16 x 8 brick (500^3), each from every 31st of the 496 projections of
+    1248x960, the finished volume delivered into device memory by the fused
+    call; the oracle evaluates 4096 sampled voxels (the last voxel among
+    them)."""
+    api = native()
+    full = synth.SCANS["full"]
+    A = oracle.carm_matrices(full)[::31]
+    vol = synth.Volume(L)
+    stack = synth.uniform_stack(len(A), full.isy, full.isx, seed=13)
+    out = torch.empty((L,) * 3, dtype=torch.float32, device="cuda")
+    with api.Backprojector(vol.L, vol.R, vol.O, full.isx, full.isy, dtype=dtype) as bp:
+        bp.add_projections_finalize(torch.from_numpy(stack).cuda(), A, out)
+        assert bp.last_path == "tma"
+    idx = np.random.default_rng(L).integers(0, L ** 3, size=4096)
+    idx[-1] = L ** 3 - 1
+    ref = oracle.backproject_voxels(vol.L, vol.R, vol.O, stack, A, idx)
+    g = out.view(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    del out
+    torch.cuda.empty_cache()
+    err = rel_l2(g, ref)
+    print(f"{L}^3 {dtype} from {len(A)} projections: sampled rel-L2 {err:.3e}")
+    assert err <= tol
 
 
 @pytest.mark.parametrize("path", [1, 2])
