@@ -145,10 +145,12 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
             kc = b.k[i];
         }
         const cudaTextureObject_t t = b.tex[i];
-        // Part 1: geometry; the y, z terms are shared by the lane's voxels.
-        const float bu = fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w));
-        const float bv = fmaf(rv.y, Y, fmaf(rv.z, Z, rv.w));
-        const float bw = fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w));
+        // Part 1: geometry; the y, z terms are shared by the lane's voxels
+        // (z outermost, y inside: the order the TMA kernel uses, which
+        // shares the y term across a lane's z values)
+        const float bu = fmaf(ru.z, Z, fmaf(ru.y, Y, ru.w));
+        const float bv = fmaf(rv.z, Z, fmaf(rv.y, Y, rv.w));
+        const float bw = fmaf(rw.z, Z, fmaf(rw.y, Y, rw.w));
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
             const float uw = fmaf(ru.x, X[k], bu);

@@ -180,13 +180,14 @@ struct TmaStage {
 // The 16 updates of one consumer lane for projection i (matrix rows ru, rv,
 // rw), reading the corner pairs from the staged tile (SMEM) or from the
 // global pair image; the two forms are separate loop bodies so neither
-// carries the other's work.  Lane voxels: X[kx] (kx = 0..3, 8 apart), Y[ky]
-// (8 apart), Z[kz] (4 apart); absolute, or offsets from the brick centre
-// with per-brick centring.
+// carries the other's work.  Lane voxels: X[kx] (kx = 0..3, 8 apart), one
+// Y, Z[kz] (kz = 0..3, adjacent); absolute, or offsets from the brick
+// centre with per-brick centring.  The row terms nest z outside y (as the
+// texture kernel does), so the y term is formed once per projection.
 template <int KIND, bool IEEE, bool SMEM>
 __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const float4 ru, const float4 rv,
                                             const float4 rw, int4 mt, uint32_t tile, const float (&X)[4],
-                                            const float (&Y)[2], const float (&Z)[2], float (&acc)[16])
+                                            const float Y, const float (&Z)[4], float (&acc)[16])
 {
     using P = Pairs<KIND>;
     using T = typename P::T;
@@ -200,12 +201,12 @@ __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const floa
     // row floor(v') + cv.
     const float off = __int_as_float(mt.y);
     const uint32_t base = tile - kIntMagicBits * (uint32_t)sizeof(T);
+    const float cu = fmaf(ru.y, Y, ru.w), cv = fmaf(rv.y, Y, rv.w), cw = fmaf(rw.y, Y, rw.w);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int ky = q >> 1, kz = q & 1;
-        const float bu = fmaf(ru.y, Y[ky], fmaf(ru.z, Z[kz], ru.w));
-        const float bv = fmaf(rv.y, Y[ky], fmaf(rv.z, Z[kz], rv.w));
-        const float bw = fmaf(rw.y, Y[ky], fmaf(rw.z, Z[kz], rw.w));
+        const float bu = fmaf(ru.z, Z[q], cu);
+        const float bv = fmaf(rv.z, Z[q], cv);
+        const float bw = fmaf(rw.z, Z[q], cw);
 #pragma unroll
         for (int kx = 0; kx < 4; ++kx) {
             const float uw = fmaf(ru.x, X[kx], bu);
@@ -266,6 +267,11 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     constexpr int kStageElems = TmaStage<KIND>::kElems;   // stage stride: 128-byte multiple
     constexpr int S = TmaBox<KIND>::S;
     constexpr int kConsumerWarps = kThreads / 32;
+    // consumer layout: 8 x-lanes by 4 y-lanes per warp, warps 0-3 and 4-7
+    // on the two 4-deep z halves; each lane 4 voxels along x (8 apart) and
+    // 4 along z, covering the brick once
+    static_assert(kBrickX == 8 * 4 && kBrickY == 4 * 4 && kBrickZ == 2 * 4 && kConsumerWarps == 8,
+                  "the consumer layout tiles a 32 x 16 x 8 brick with 8 warps");
     extern __shared__ __align__(128) unsigned char dyn_smem[];   // the ring: S stages of kStageElems pairs
     T (*buf)[kStageElems] = reinterpret_cast<T (*)[kStageElems]>(dyn_smem);
     __shared__ __align__(8) uint64_t full[S], empty[S];
@@ -349,29 +355,30 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     }
 
     // ---------------- consumers
-    const int tx = lane & 7, tz = lane >> 3;
-    // this lane's voxels: x0 + {0, 8, 16, 24}, y0 + {0, 8}, z0 + {0, 4};
+    // A warp is 8 lanes along x by 4 along y in one z plane of the brick:
+    // its 32 voxels land on about the same detector rows, spread along
+    // them, which keeps the shared-memory bank conflicts of the corner loads
+    // low (a z-spread warp spans rows whose pitch aliases the banks).
+    const int tx = lane & 7, ty = lane >> 3;
+    // this lane's voxels: x0 + {0, 8, 16, 24}, y0, z0 + {0, 1, 2, 3};
     // lanes beyond a ragged edge compute with the last voxel's coordinates
     // (inside the brick box, so their loads stay in the staged tile) and
     // store nothing
     // (BLK: offsets from the centre of the brick's voxel box clipped to the
     // volume, (x0 + x1) / 2 etc., a multiple of 1/2, as in the pre-pass)
-    const int x0 = bx0 + tx, y0 = by0 + warp, z0 = bz0 + tz;
+    const int x0 = bx0 + tx, y0 = by0 + 4 * (warp & 3) + ty, z0 = bz0 + 4 * (warp >> 2);
     const float hx = 0.5f * (float)(bx0 + min(bx0 + kBrickX, L) - 1);
     const float hy = 0.5f * (float)(by0 + min(by0 + kBrickY, L) - 1);
     const float hz = 0.5f * (float)(bz0 + min(bz0 + kBrickZ, g.Lz) - 1);
-    float X[4], Y[2], Z[2];
+    float X[4], Z[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int x = min(x0 + 8 * k, L - 1);
+        const int x = min(x0 + 8 * k, L - 1), z = min(z0 + k, g.Lz - 1);
         X[k] = BLK ? g.R * ((float)x - hx) : fmaf(g.R, (float)x, g.Ox);
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int y = min(y0 + 8 * k, L - 1), z = min(z0 + 4 * k, g.Lz - 1);
-        Y[k] = BLK ? g.R * ((float)y - hy) : fmaf(g.R, (float)y, g.Oy);
         Z[k] = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)z, g.Oz);
     }
+    const int yc = min(y0, L - 1);
+    const float Y = BLK ? g.R * ((float)yc - hy) : fmaf(g.R, (float)yc, g.Oy);
 
     float acc[16];
 #pragma unroll
@@ -425,7 +432,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     float *const fin = b.final_out;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int y = y0 + 8 * (q >> 1), z = z0 + 4 * (q & 1);
+        const int y = y0, z = z0 + q;
         if (y >= L || z >= g.Lz)
             continue;
         const size_t r0 = ((size_t)z * L + y) * L;
