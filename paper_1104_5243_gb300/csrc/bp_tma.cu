@@ -139,13 +139,22 @@ struct Pairs<kPairF32> {
     __device__ static float2 load(uint32_t a) { return lds_f2<OFF>(a); }
 };
 
+// 16-bit pairs unpack to (left, right - left) as well: the left pixel
+// widened to float32, and the difference by one mixed-precision subtraction
+// (the 16-bit right pixel widened exactly, minus the float32 left, rounded
+// once: the float32 subtraction the texture kernel performs on the same two
+// widened values).
 template <>
 struct Pairs<kPairF16> {
     using T = unsigned int;
-    static constexpr bool kDiff = false;
+    static constexpr bool kDiff = true;
     __device__ static float2 unpack(unsigned int p)
     {
-        return __half22float2(*reinterpret_cast<const __half2 *>(&p));
+        float l, d;
+        asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.f16 %0, lo;\n\t"
+            "sub.rn.f32.f16 %1, hi, %0;\n\t}"
+            : "=f"(l), "=f"(d) : "r"(p));
+        return make_float2(l, d);
     }
     template <int OFF>
     __device__ static float2 load(uint32_t a) { return unpack(lds_u32<OFF>(a)); }
@@ -154,10 +163,14 @@ struct Pairs<kPairF16> {
 template <>
 struct Pairs<kPairBF16> {
     using T = unsigned int;
-    static constexpr bool kDiff = false;
+    static constexpr bool kDiff = true;
     __device__ static float2 unpack(unsigned int p)
     {
-        return make_float2(__uint_as_float(p << 16), __uint_as_float(p & 0xffff0000u));
+        float l, d;
+        asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.bf16 %0, lo;\n\t"
+            "sub.rn.f32.bf16 %1, hi, %0;\n\t}"
+            : "=f"(l), "=f"(d) : "r"(p));
+        return make_float2(l, d);
     }
     template <int OFF>
     __device__ static float2 load(uint32_t a) { return unpack(lds_u32<OFF>(a)); }
