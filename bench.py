@@ -56,8 +56,8 @@ UNIT = "GUP/s"
 FP32_PER_SM_CLK = 128.0
 FP32_INSTR_PER_UPDATE = 20.5
 ISSUE_PER_SM_CLK = 128.0
-INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 28.5, ("tma", "f16"): 34.4,
-                    ("tma", "bf16"): 34.4}
+INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 28.5, ("tma", "f16"): 32.4,
+                    ("tma", "bf16"): 32.4}
 MUFU_PER_SM_CLK = 16.0
 SMEM_BYTES_PER_SM_CLK = 128.0
 # Adjoint tile kernel (bp_adjoint_smem_kernel), 256^3 -> 248 x 624x480:
