@@ -493,3 +493,18 @@ def test_paper_metric_facts():
     assert per_sweep * f["n_proj"] / 2 ** 30 == pytest.approx(f["all_proj_gb"], rel=1e-12)
     f = facts["projection_stack"]
     assert f["n_proj"] * f["isx"] * f["isy"] * 4 / 1e9 == pytest.approx(f["gb"], abs=0.05)
+
+
+def test_error_measures_closed_forms():
+    """Sect. 7.2's PSNR and the relative L2 error on cases with closed forms:
+    a reference spanning [2, 10] (M = 8) and a reconstruction off by a
+    constant 0.01 give 10 log10(64 / 1e-4) = 58.06 dB; a reconstruction off
+    by alternating +-0.5 on a reference of constant 4 gives rel-L2 1/8."""
+    R = np.linspace(2.0, 10.0, 1001)
+    assert oracle.psnr(R + 0.01, R) == pytest.approx(10.0 * math.log10(64.0 / 1e-4), abs=1e-9)
+    assert oracle.psnr(R, R) == float("inf")
+    # the PSNR does not depend on where the reference's range sits
+    assert oracle.psnr(R + 100.01, R + 100.0) == pytest.approx(oracle.psnr(R + 0.01, R), abs=1e-6)
+    ref = np.full(1000, 4.0)
+    got = ref + 0.5 * np.where(np.arange(1000) % 2 == 0, 1.0, -1.0)
+    assert oracle.rel_l2(got, ref) == pytest.approx(0.125, rel=1e-12)
