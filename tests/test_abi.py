@@ -64,6 +64,8 @@ def test_null_context_is_rejected(lib):
     assert lib.bp_add_projections(None, None, 0, None, 1) == N.BP_EINVAL
     assert lib.bp_finalize(None, None, 0) == N.BP_EINVAL
     assert lib.bp_adjoint(None, None, 0, None, 1, None, 0) == N.BP_EINVAL
+    assert lib.bp_add_projections_finalize(None, None, 0, None, 1, None, 0) == N.BP_EINVAL
+    assert "bp_add_projections_finalize" in N.bp_last_error(None)
     assert lib.bp_set_option(None, 1, 0) == N.BP_EINVAL
     assert lib.bp_destroy(None) == N.BP_OK
 
