@@ -148,6 +148,16 @@ def ncu_fields(kernel_file: str, profile: str, names) -> dict | None:
         return None
 
 
+def hbm_peak_gbs() -> tuple[float, str]:
+    """HBM bandwidth peak: the measured copy figure of MEASURED_PEAKS.json
+    when present, else 6800 GB/s (one earlier measurement on a GB300)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError, TypeError):
+        return 6800.0, "fallback"
+
+
 def ncu_traffic(kernel_file: str, profile: str):
     """DRAM bytes per launch from a committed ncu summary (None as ncu_fields)."""
     f = ncu_fields(kernel_file, profile, ["traffic_bytes_per_launch"])
@@ -587,6 +597,10 @@ def main():
     traffic = ncu_traffic(ksrc, f"{kname}_{head}_{args.L}.md") if args.n_proj == 496 and nz == args.L else None
     ncu_pct = ncu_fields(ksrc, f"{kname}_{head}_{args.L}x64.md", NCU_FRACTIONS)
     basis = ("shared-memory bandwidth" if head_path == "tma" else "measured texture gather rate")
+    alg_bytes = algorithmic_bytes(vol.L, min(scan.n, 64), scan.isx, scan.isy, head, head_path,
+                                  k["computed_fraction"], nz)
+    avg_ms = k["kernel_ms"] / max(k["launches"], 1)
+    hbm_peak, hbm_src = hbm_peak_gbs()
     roofline = {
         "bound": "alu", "unit": UNIT, "kernel": f"{kname} ({head} projections, {head_path} path)",
         "achieved": round(achieved, 2) if achieved else None,
@@ -604,8 +618,14 @@ def main():
         "traffic": traffic,
         "ncu_pct_of_peak": (dict(ncu_pct, profile=f"profiles/{kname}_{head}_{args.L}x64.md")
                             if ncu_pct else None),
-        "algorithmic_bytes_per_launch": algorithmic_bytes(vol.L, min(scan.n, 64), scan.isx, scan.isy, head,
-                                                          head_path, k["computed_fraction"], nz),
+        "algorithmic_bytes_per_launch": alg_bytes,
+        # DRAM side (not the bound): bytes per launch over the average launch
+        # time, against the HBM peak
+        "hbm": {"algorithmic_gbs": round(alg_bytes / (avg_ms / 1e3) / 1e9, 1),
+                "traffic_gbs": round(traffic / (avg_ms / 1e3) / 1e9, 1) if traffic else None,
+                "peak_gbs": hbm_peak, "peak_source": hbm_src,
+                "frac_algorithmic": round(alg_bytes / (avg_ms / 1e3) / 1e9 / hbm_peak, 4),
+                "frac_traffic": round(traffic / (avg_ms / 1e3) / 1e9 / hbm_peak, 4) if traffic else None},
     }
     cpu = None
     if not args.no_cpu_baseline:

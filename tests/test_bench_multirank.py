@@ -153,3 +153,14 @@ def test_ncu_fields_need_every_name_and_the_current_source(tmp_path, monkeypatch
     assert bench.ncu_fields("k.cu", "p.md", ["fma_pipe_pct", "smem_wavefronts_pct"]) is None
     (root / "paper_1104_5243_gb300" / "csrc" / "k.cu").write_bytes(b"changed")
     assert bench.ncu_fields("k.cu", "p.md", ["fma_pipe_pct"]) is None
+
+
+def test_hbm_peak_prefers_the_measured_file(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.hbm_peak_gbs() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6786.2}))
+    assert bench.hbm_peak_gbs() == (6786.2, "measured")
+    (tmp_path / "MEASURED_PEAKS.json").write_text("{}")
+    assert bench.hbm_peak_gbs() == (6800.0, "fallback")
