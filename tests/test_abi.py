@@ -99,3 +99,18 @@ def test_create_slab_validates_the_slab_without_the_gpu(lib):
         st = lib.bp_create_slab(ctypes.byref(h), L, nz, z0, 1.0, ctypes.cast(O, ctypes.c_void_p), 8, 8, 0, None)
         assert st == N.BP_EINVAL, (L, nz, z0)
         assert h.value is None
+
+
+def test_slab_reconstruction_validates_its_arguments_without_the_gpu():
+    """backproject_slabs refuses a slab of no slices and an output that is not
+    a contiguous (L, L, L) float32 host tensor before any device work."""
+    torch = pytest.importorskip("torch")
+    from paper_1104_5243_gb300 import api
+    imgs = torch.zeros((1, 4, 4))
+    A = [[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 1]]]
+    with pytest.raises(ValueError):
+        api.backproject_slabs(8, 1.0, [0, 0, 0], imgs, A, slab=0)
+    with pytest.raises(ValueError):
+        api.backproject_slabs(8, 1.0, [0, 0, 0], imgs, A, slab=4, out=torch.zeros((8, 8, 7)))
+    with pytest.raises(ValueError):
+        api.backproject_slabs(8, 1.0, [0, 0, 0], imgs, A, slab=4, out=torch.zeros((8, 8, 8), dtype=torch.float64))

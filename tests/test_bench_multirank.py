@@ -164,3 +164,24 @@ def test_hbm_peak_prefers_the_measured_file(tmp_path, monkeypatch):
     assert bench.hbm_peak_gbs() == (6786.2, "measured")
     (tmp_path / "MEASURED_PEAKS.json").write_text("{}")
     assert bench.hbm_peak_gbs() == (6800.0, "fallback")
+
+
+def test_algorithmic_bytes_of_a_launch():
+    """Bytes one mid-step launch must move (the roofline's unit): the volume
+    read and written once, each projection's pair image once (f32 pairs of
+    8 B, pitch rounded to 2 pairs; 16-bit pairs of 4 B, pitch rounded to 4),
+    and for f32 the 48-byte centring record of every computed (brick,
+    projection) pair."""
+    sys.path.insert(0, ROOT)
+    import bench
+    L, n, isx, isy = 512, 64, 1248, 960
+    bricks = 16 * 32 * 64
+    f32 = bench.algorithmic_bytes(L, n, isx, isy, "f32", "tma", 0.75)
+    assert f32 == 8 * L ** 3 + n * 1250 * isy * 8 + int(48 * n * bricks * 0.75)
+    f16 = bench.algorithmic_bytes(L, n, isx, isy, "f16", "tma", 0.75)
+    assert f16 == 8 * L ** 3 + n * 1252 * isy * 4
+    # a z-slab of 64 slices: an eighth of the volume and of the bricks
+    slab = bench.algorithmic_bytes(L, n, isx, isy, "f32", "tma", 0.75, Lz=64)
+    assert slab == 8 * L * L * 64 + n * 1250 * isy * 8 + int(48 * n * (bricks // 8) * 0.75)
+    tex = bench.algorithmic_bytes(L, n, isx, isy, "f32", "texture", 1.0)
+    assert tex == 8 * L ** 3 + n * isx * isy * 4 + 48 * n * (16 * 64 * 128)
