@@ -579,6 +579,43 @@ def main():
             "workload": "8 phantoms, 128^3 x 120 x 312x240, forward + backward + Adam",
             "ms_per_step": round((time.perf_counter() - t) / args.steps * 1e3, 2),
             "note": "includes generating the phantom batch on the GPU once per call"}
+        # CGLS on the adjoint's workload: per iteration one forward model
+        # (B^T) and one transpose (B) through the library, plus the vector
+        # updates; (K + 1 iterations - 1 iteration) / K removes the initial
+        # transpose
+        from paper_1104_5243_gb300 import iterative
+        bp = api.Backprojector(vh.L, vh.R, vh.O, half.isx, half.isy)
+        ops = iterative.Operators(bp, Ah, iterative.model_scale(vh.R, api.iso_pitch(half)))
+        pdata = ops.forward(fvol)
+        iterative.cgls(ops, pdata, 1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        iterative.cgls(ops, pdata, 1)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter() - t
+        t = time.perf_counter()
+        iterative.cgls(ops, pdata, args.steps + 1)
+        torch.cuda.synchronize()
+        cg_ms = (time.perf_counter() - t - t1) / args.steps * 1e3
+        bp.close()
+        extra["cgls_iteration"] = {"workload": "256^3 x 248 x 624x480, one B^T and one B per iteration",
+                                   "ms_per_iteration": round(cg_ms, 3),
+                                   "gups": round(2 * 256 ** 3 * half.n / (cg_ms / 1e3) / 1e9, 1)}
+        # A 512^3 volume reconstructed slab by slab (4 slabs of 128 slices,
+        # a context each) into pinned host memory, from the device stack
+        big = torch.empty((args.L,) * 3, dtype=torch.float32).pin_memory()
+        slab = max(8, args.L // 4)
+        api.backproject_slabs(args.L, vol.R, vol.O, stack, A, slab=slab, out=big)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        api.backproject_slabs(args.L, vol.R, vol.O, stack, A, slab=slab, out=big)
+        torch.cuda.synchronize()
+        sl_s = time.perf_counter() - t
+        extra["slab_reconstruction"] = {
+            "workload": f"{args.L}^3 x {scan.n} x {scan.isx}x{scan.isy} in slabs of {slab} slices into pinned "
+                        "host memory (context creation included)",
+            "ms": round(sl_s * 1e3, 2), "gups": round(args.L ** 3 * scan.n / sl_s / 1e9, 1)}
+        del big
 
     if rank != 0:
         if dist is not None:
