@@ -79,6 +79,7 @@ struct bp_ctx {
     int *err_dev = nullptr;        // set by a kernel whose bounded wait gave up
     bool cull = true;              // BP_OPT_CULL
     bool host_direct = true;       // BP_OPT_HOST_DIRECT (f32 host images: copy engine into arrays)
+    bool arrays_ready = false;     // texture path's arrays allocated (ensure_arrays)
     unsigned long long *work_dev = nullptr;   // updates computed by culled launches
     unsigned long long work_host = 0;         // updates of launches without culling
     // texture path, per input set: per-block visibility masks and
@@ -167,6 +168,8 @@ static void release(bp_ctx *c)
 
 static bp_status alloc_slot(bp_ctx *c, int s, int j)
 {
+    if (c->arr[s][j] != nullptr)
+        return BP_OK;   // allocated by an earlier (possibly interrupted) pass
     cudaChannelFormatDesc fmt;
     if (c->dtype == BP_F32)
         fmt = cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);
@@ -188,6 +191,23 @@ static bp_status alloc_slot(bp_ctx *c, int s, int j)
     td.normalizedCoords = 0;
     CTX_CK(c, cudaCreateTextureObject(&c->tex[s][j], &res, &td, nullptr));
     CTX_CK(c, cudaCreateSurfaceObject(&c->surf[s][j], &res));
+    return BP_OK;
+}
+
+// The texture path's projection arrays (two sets of kMaxBatch, with their
+// texture and surface objects), allocated on the path's first use: the
+// default TMA path never touches them.
+static bp_status ensure_arrays(bp_ctx *c)
+{
+    if (c->arrays_ready)
+        return BP_OK;
+    for (int s = 0; s < 2; ++s)
+        for (int j = 0; j < kMaxBatch; ++j) {
+            const bp_status st = alloc_slot(c, s, j);
+            if (st != BP_OK)
+                return st;
+        }
+    c->arrays_ready = true;
     return BP_OK;
 }
 
@@ -246,12 +266,6 @@ static bp_status create_context(bp_ctx **out, int L, int nz, int z0, double R, c
         check(cudaMemsetAsync(c->work_dev, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync");
     if (st == BP_OK)
         check(cudaMemsetAsync(c->vol, 0, nvox * sizeof(float), c->stream), "cudaMemsetAsync");
-    for (int s = 0; s < 2 && st == BP_OK; ++s)
-        for (int j = 0; j < kMaxBatch && st == BP_OK; ++j) {
-            bp_status r = alloc_slot(c, s, j);
-            if (r != BP_OK)
-                st = fail(nullptr, r, "bp_create: %s", c->err);
-        }
     if (st == BP_OK)
         check(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     if (st != BP_OK) {
@@ -495,11 +509,9 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
         // texture unit's data return bounds 32-bit gathers; bf16 1249
         // against 1198; f16 1220-1270 against 1240).
         const bool tma = c->path != 1;
-        if (tma) {
-            st = ensure_pairs(c);
-            if (st != BP_OK)
-                return st;
-        }
+        st = tma ? ensure_pairs(c) : ensure_arrays(c);
+        if (st != BP_OK)
+            return st;
         const int s = c->next_set;
         c->next_set ^= 1;
         CTX_CK(c, cudaStreamWaitEvent(c->copy_stream, c->kern_done[s], 0));
