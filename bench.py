@@ -658,11 +658,12 @@ def main():
         "algorithmic_bytes_per_launch": alg_bytes,
         # DRAM side (not the bound): bytes per launch over the average launch
         # time, against the HBM peak
-        "hbm": {"algorithmic_gbs": round(alg_bytes / (avg_ms / 1e3) / 1e9, 1),
-                "traffic_gbs": round(traffic / (avg_ms / 1e3) / 1e9, 1) if traffic else None,
-                "peak_gbs": hbm_peak, "peak_source": hbm_src,
-                "frac_algorithmic": round(alg_bytes / (avg_ms / 1e3) / 1e9 / hbm_peak, 4),
-                "frac_traffic": round(traffic / (avg_ms / 1e3) / 1e9 / hbm_peak, 4) if traffic else None},
+        "hbm": ({"algorithmic_gbs": round(alg_bytes / (avg_ms / 1e3) / 1e9, 1),
+                 "traffic_gbs": round(traffic / (avg_ms / 1e3) / 1e9, 1) if traffic else None,
+                 "peak_gbs": hbm_peak, "peak_source": hbm_src,
+                 "frac_algorithmic": round(alg_bytes / (avg_ms / 1e3) / 1e9 / hbm_peak, 4),
+                 "frac_traffic": round(traffic / (avg_ms / 1e3) / 1e9 / hbm_peak, 4) if traffic else None}
+                if avg_ms > 0 else None),
     }
     cpu = None
     if not args.no_cpu_baseline:
