@@ -34,50 +34,77 @@ METRIC = "GUP/s at 512³×496 proj: FP32 vs FP16-projection form, % of roofline"
 UNIT = "GUP/s"
 
 # Roofline of the backprojection kernels (one update = one voxel x one
-# projection), per SM per clock, times SMs and the SM clock sampled under load.
-# Both kernels:
-#   fp32_pipe: 128 FP32 lanes over 20.5 FP32-pipe instructions per update
-#     (from the source: 3 FFMA geometry + 1.5 FFMA of y/z terms per 4 voxels,
-#     2 FMUL u/v, 2 floor, 2 FADD/FFMA gather coordinate or tile index,
-#     2 FADD fractions, 3 FADD + 3 FFMA interpolation, 1 FMUL + 1 FFMA weight
-#     and accumulate);
+# projection), from the METHOD's work per update, per SM per clock, times the
+# SMs and the SM clock sampled under load.  Every bound below is derivable
+# from the per-update operation counts of Sect. 3.1-3.2 and the unit counts of
+# the GPU; nothing in them comes from a profile of the kernel, so overhead the
+# kernel adds cannot raise its peak.
+#   fp32_pipe: 128 FP32 lanes per SM over the 20.5 FP32-pipe operations an
+#     update needs with FMA and incremental stepping: 3 FFMA geometry + 1.5
+#     FFMA of the y/z terms per 4 voxels, 2 FMUL u/v, 2 floor, 2 FADD/FFMA
+#     gather coordinate, 2 FADD fractions, 3 FADD + 3 FFMA bilinear
+#     interpolation, 1 FMUL + 1 FFMA weight and accumulate (the paper's 31
+#     flop, Sect. 3.2, with the multiply-adds fused);
 #   mufu: 16 reciprocals per SM per clock, one per update;
-#   issue: 128 thread instructions per SM per clock over the instructions per
-#     computed update ncu counts for the kernel (smsp__inst_executed x 32 /
-#     computed updates; profiles/<kernel>_<form>_512x64.md).
-# Texture kernel (bp_fwd_kernel):
-#   gather: the texture unit's 2x2-gather rate for the storage type, MEASURED
-#     on this GPU by bp_probe_gather (one gather per update).
-# TMA kernel (bp_tma_kernel):
-#   smem: 128 B per SM per clock of shared-memory bandwidth over the bytes an
-#     update moves: two pair loads (8-byte float32 pairs, 4-byte 16-bit ones),
-#     plus the TMA fill of the box (114 x 36 float32 pairs, 100 x 36 16-bit
-#     ones) per 32 x 16 x 8-voxel brick and projection: 24.0 B (f32), 11.5 B.
+#   smem (TMA path): 128 B per SM per clock of shared-memory bandwidth over
+#     the 4 projection texels an update reads: 16 B for float32 storage, 8 B
+#     for 16-bit storage;
+#   gather (texture path): the texture unit's 2x2-gather rate for the storage
+#     type, MEASURED on this GPU by bp_probe_gather (one gather per update).
 FP32_PER_SM_CLK = 128.0
 FP32_INSTR_PER_UPDATE = 20.5
+MUFU_PER_SM_CLK = 16.0
+SMEM_BYTES_PER_SM_CLK = 128.0
+TEXELS_PER_UPDATE = 4
+# Diagnostics only (they explain where a kernel loses time; they are not its
+# roofline): instruction issue at the instructions per computed update that
+# ncu counts for the kernel (smsp__inst_executed x 32 / computed updates;
+# profiles/<kernel>_<form>_512x64.md), and shared-memory bandwidth including
+# the TMA fill of each brick's box.
 ISSUE_PER_SM_CLK = 128.0
 INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 28.5, ("tma", "f16"): 32.4,
                     ("tma", "bf16"): 32.4}
-MUFU_PER_SM_CLK = 16.0
-SMEM_BYTES_PER_SM_CLK = 128.0
-# Adjoint tile kernel (bp_adjoint_smem_kernel), 256^3 -> 248 x 624x480:
-#   issue: ncu's instructions per update (profiles/bp_adjoint_smem_kernel_256.md);
-#   smem_atomics: four shared-memory atomics per update, each warp instruction
-#     taking the wavefronts ncu measures (bank conflicts included: 32
-#     scattered addresses over 32 banks), one wavefront per SM per clock.
+# Adjoint (B^T, the same arithmetic per update as B, with the four corner
+# terms scattered instead of gathered):
+#   fp32_pipe: the forward's 20.5 FP32-pipe operations (geometry, floor,
+#     fractions, four bilinear weights, 1/w^2);
+#   smem_atomics: four shared-memory atomics per update, conflict-free (one
+#     wavefront per warp instruction, one wavefront per SM per clock);
+#   mufu: one reciprocal per update.
+# Diagnostics: ncu's instructions per update and wavefronts per atomic
+# instruction (profiles/bp_adjoint_smem_kernel_256.md).
+ADJ_ATOMICS_PER_UPDATE = 4
 ADJ_INSTR_PER_UPDATE = 50.0
 ADJ_ATOMIC_WAVEFRONTS = 3.7
 
 
 def adjoint_roofline_gups(sm_mhz: float, sms: int) -> dict:
     f = sm_mhz * 1e6
-    bounds = {"issue": sms * ISSUE_PER_SM_CLK / ADJ_INSTR_PER_UPDATE * f / 1e9,
-              "smem_atomics": sms / (4 * ADJ_ATOMIC_WAVEFRONTS / 32) * f / 1e9}
+    bounds = {"fp32_pipe": sms * FP32_PER_SM_CLK / FP32_INSTR_PER_UPDATE * f / 1e9,
+              "smem_atomics": sms * 32.0 / ADJ_ATOMICS_PER_UPDATE * f / 1e9,
+              "mufu": sms * MUFU_PER_SM_CLK * f / 1e9}
     bounds["min"] = min(bounds.values())
     return bounds
 
 
+def adjoint_diagnostics_gups(sm_mhz: float, sms: int) -> dict:
+    """Rates the adjoint kernel as built could reach if issue or its bank
+    conflicts alone bound it (from its ncu profile; not the roofline)."""
+    f = sm_mhz * 1e6
+    return {"issue_at_measured_instr": sms * ISSUE_PER_SM_CLK / ADJ_INSTR_PER_UPDATE * f / 1e9,
+            "smem_atomics_at_measured_wavefronts":
+                sms / (ADJ_ATOMICS_PER_UPDATE * ADJ_ATOMIC_WAVEFRONTS / 32) * f / 1e9,
+            "instr_per_update": ADJ_INSTR_PER_UPDATE, "wavefronts_per_atomic": ADJ_ATOMIC_WAVEFRONTS}
+
+
+def texel_bytes_per_update(form: str) -> float:
+    """Projection bytes an update reads: four texels of the storage type."""
+    return TEXELS_PER_UPDATE * (4 if form == "f32" else 2)
+
+
 def tma_smem_bytes_per_update(form: str) -> float:
+    """Shared-memory bytes per update of the TMA kernel as built (two pair
+    loads plus the box fill per 32 x 16 x 8 brick); a diagnostic."""
     pair, bu = (8, 114) if form == "f32" else (4, 100)
     return 2.0 * pair + bu * 36 * pair / (32 * 16 * 8)
 
@@ -89,14 +116,26 @@ def roofline_peak_gups(path: str, form: str, sm_mhz: float, sms: int, gather_per
         "mufu": sms * MUFU_PER_SM_CLK * f / 1e9,
     }
     if path == "tma":
-        bounds["smem"] = sms * SMEM_BYTES_PER_SM_CLK / tma_smem_bytes_per_update(form) * f / 1e9
+        bounds["smem"] = sms * SMEM_BYTES_PER_SM_CLK / texel_bytes_per_update(form) * f / 1e9
     else:
         bounds["gather"] = sms * gather_per_sm_clk * f / 1e9
-    instr = INSTR_PER_UPDATE.get((path, form))
-    if instr is not None:
-        bounds["issue"] = sms * ISSUE_PER_SM_CLK / instr * f / 1e9
     bounds["min"] = min(bounds.values())
     return bounds
+
+
+def roofline_diagnostics_gups(path: str, form: str, sm_mhz: float, sms: int) -> dict:
+    """What the kernel as built is limited by (from its ncu profile): issue at
+    its measured instructions per update, and for the TMA path shared-memory
+    bandwidth including the box fill.  Explains a fraction; not the peak."""
+    f = sm_mhz * 1e6
+    d = {}
+    instr = INSTR_PER_UPDATE.get((path, form))
+    if instr is not None:
+        d["issue_at_measured_instr"] = sms * ISSUE_PER_SM_CLK / instr * f / 1e9
+        d["instr_per_update"] = instr
+    if path == "tma":
+        d["smem_with_box_fill"] = sms * SMEM_BYTES_PER_SM_CLK / tma_smem_bytes_per_update(form) * f / 1e9
+    return d
 
 
 def algorithmic_bytes(L: int, n: int, isx: int, isy: int, form: str, path: str, computed_fraction: float,
@@ -388,6 +427,73 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def link_rates(host_src, dev_dst, host_dst, dev_src, stream) -> dict:
+    """Host-to-device and device-to-host copy rates (GB/s) on the end-to-end
+    step's own pinned buffers, in the same run: the projection stack up, the
+    volume down, two copies each, CUDA events on the stream."""
+    import torch
+    out = {}
+    for name, dst, src in (("h2d_gbs", dev_dst, host_src), ("d2h_gbs", host_dst, dev_src)):
+        n = min(dst.numel(), src.numel())
+        d, s_ = dst.view(-1)[:n], src.view(-1)[:n]
+        d.copy_(s_, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(2):
+            d.copy_(s_, non_blocking=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = round(2 * n * 4 / (t0.elapsed_time(t1) / 1e3) / 1e9, 1)
+    return out
+
+
+def time_volume(api, N, L: int, scan, stack, A, form: str, warmup: int, steps: int, stream) -> dict:
+    """GUP/s of the device-resident step at another volume size: nominal
+    updates over the step time, and over the backprojection kernels' event
+    time (nominal and computed updates), with the path and brick depth the
+    library chose."""
+    import torch
+    from paper_1104_5243_gb300 import synth
+    vol = synth.Volume(L)
+    out = torch.empty((L, L, L), dtype=torch.float32, device="cuda")
+    bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=form)
+
+    def step():
+        bp.reset()
+        bp.add_projections(stack, A)
+        bp.finalize(out)
+
+    for _ in range(warmup):
+        step()
+    bp.set_option(N.BP_OPT_TIMING, 1)
+    bp.kernel_stats()
+    c0 = bp.query(N.BP_QUERY_UPDATES_COMPUTED)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    launches, kms = bp.kernel_stats()
+    computed = (bp.query(N.BP_QUERY_UPDATES_COMPUTED) - c0) / steps
+    nominal = L ** 3 * scan.n
+    res = {"gups": round(nominal / (ms / 1e3) / 1e9, 2), "ms_per_step": round(ms, 3),
+           "kernel_gups": round(nominal / (kms / steps / 1e3) / 1e9, 2),
+           "kernel_gups_computed": round(computed / (kms / steps / 1e3) / 1e9, 2),
+           "computed_fraction": round(computed / nominal, 4), "path": bp.last_path,
+           "brick_depth": bp.query(N.BP_QUERY_LAST_BRICK_DEPTH) if bp.last_path == "tma" else None,
+           "steps": steps}
+    bp.close()
+    del out
+    torch.cuda.empty_cache()
+    return res
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -463,6 +569,7 @@ def main():
     forms = {}
     kernel = {}
     path_taken = {}
+    depth_taken = {}
     clocks = None
     rcp_modes = None
     for form in args.forms.split(","):
@@ -492,6 +599,7 @@ def main():
         launches, kms = bp.kernel_stats()
         computed = bp.query(N.BP_QUERY_UPDATES_COMPUTED) - computed0
         path_taken[form] = bp.last_path
+        depth_taken[form] = bp.query(N.BP_QUERY_LAST_BRICK_DEPTH)
         bp.set_option(N.BP_OPT_TIMING, 0)
         gups = whole_job_gups(job_updates, args.steps, 1, ms)
         forms[form] = {"value": round(gups, 2), "ms_per_step": round(ms / args.steps, 3)}
@@ -527,11 +635,26 @@ def main():
         torch.cuda.synchronize()
         wall = rank_max(time.perf_counter() - t0)
         bp.close()
+        link = link_rates(stack_host, stack, vol_host, out, stream)
         e2e = {"value": round(whole_job_gups(job_updates, args.steps, 1, wall * 1e3), 2), "unit": UNIT,
+               "link": link,
                "h2d_bytes_per_step": int(stack_host.numel() * 4),
                "d2h_bytes_per_step": int(vol_host.numel() * 4),
                "step": "reset + bp_add_projections_finalize (pinned host images in, finished volume into "
                        "pinned host memory)"}
+
+    # The other volume sizes of the full-scale and precision workloads
+    # (256^3: 1 mm voxels, and 1024^3: 0.25 mm, from the same 496
+    # projections of 1248x960), f32 and f16 storage, device-resident,
+    # timed like the headline (kernel events on the context's stream).
+    sizes = {}
+    if not args.no_extra and args.split == "replica" and args.n_proj == 496:
+        for L2 in (256, 1024):
+            if L2 == args.L:
+                continue
+            sizes[str(L2)] = {f: time_volume(api, N, L2, scan, stack, A, f, 3, 2 if L2 > 512 else args.steps,
+                                             stream)
+                              for f in ("f32", "f16")}
 
     # The other two timed paths of the method: the adjoint (B^T, the autograd
     # backward) on the differentiation workload, 256^3 -> 248 x 624x480, and
@@ -559,15 +682,21 @@ def main():
         bp.close()
         agups = 256 ** 3 * half.n / (ams / 1e3) / 1e9
         abounds = adjoint_roofline_gups((clocks or {}).get("sm_mhz") or 2070.0, sms)
+        abind = min((k for k in abounds if k != "min"), key=lambda k: abounds[k])
         extra["adjoint"] = {"workload": "B^T 256^3 -> 248 x 624x480", "ms_per_call": round(ams, 3),
                             "gups": round(agups, 2),
-                            "roofline": {"bound": "smem_atomics" if abounds["min"] == abounds["smem_atomics"]
-                                         else "issue", "achieved": round(agups, 2),
+                            "roofline": {"bound": abind, "achieved": round(agups, 2),
                                          "peak": round(abounds["min"], 1), "unit": UNIT,
                                          "frac": round(agups / abounds["min"], 4),
                                          "bounds_gups": {k: round(v, 1) for k, v in abounds.items()},
+                                         "peak_basis": "min(FP32 pipe at 20.5 FP32 operations per update, "
+                                                       "4 conflict-free shared-memory atomics per update, MUFU) "
+                                                       "x SMs x sampled SM clock",
                                          "note": "achieved is per call (4 launches, the output zeroing "
-                                                 "and the centring pre-pass included)"}}
+                                                 "and the centring pre-pass included)"},
+                            "diagnostics": {k: round(v, 1) for k, v in
+                                            adjoint_diagnostics_gups((clocks or {}).get("sm_mhz") or 2070.0,
+                                                                     sms).items()}}
         from paper_1104_5243_gb300 import learned as lm
         torch.manual_seed(0)
         lm.train(steps=args.warmup, batch=8)
@@ -633,23 +762,29 @@ def main():
     kname, ksrc = ("bp_tma_kernel", "bp_tma.cu") if head_path == "tma" else ("bp_fwd_kernel", "bp_fwd.cu")
     traffic = ncu_traffic(ksrc, f"{kname}_{head}_{args.L}.md") if args.n_proj == 496 and nz == args.L else None
     ncu_pct = ncu_fields(ksrc, f"{kname}_{head}_{args.L}x64.md", NCU_FRACTIONS)
-    basis = ("shared-memory bandwidth" if head_path == "tma" else "measured texture gather rate")
+    basis = ("shared-memory bandwidth" if head_path == "tma" else "the measured texture gather rate")
     alg_bytes = algorithmic_bytes(vol.L, min(scan.n, 64), scan.isx, scan.isy, head, head_path,
                                   k["computed_fraction"], nz)
     avg_ms = k["kernel_ms"] / max(k["launches"], 1)
     hbm_peak, hbm_src = hbm_peak_gbs()
+    bind = min((kk for kk in peak if kk != "min"), key=lambda kk: peak[kk])
     roofline = {
         "bound": "alu", "unit": UNIT, "kernel": f"{kname} ({head} projections, {head_path} path)",
         "achieved": round(achieved, 2) if achieved else None,
         "peak": round(peak["min"], 1),
         "frac": round(achieved / peak["min"], 4) if achieved else None,
-        "peak_basis": f"min({basis}, instruction issue, FP32 pipe, MUFU) x SMs x sampled "
-                      "SM clock; achieved counts the updates computed (culled blocks excluded)",
+        "binding": bind,
+        "peak_basis": f"min(FP32 pipe at {FP32_INSTR_PER_UPDATE} FP32 operations per update, "
+                      f"{basis} at the 4 texels an update reads, MUFU) x SMs x sampled SM clock "
+                      "(derived from unit counts and clocks; no profile of the kernel enters it); "
+                      "achieved counts the updates computed (culled bricks excluded)",
         "achieved_nominal": round(k["kernel_gups"], 2),
         "computed_fraction": round(k["computed_fraction"], 4),
         "peak_at_sm_mhz": sm_mhz,
         "gather_per_sm_clk_measured": {f: round(v, 3) for f, v in gather_rate.items()},
         "bounds_gups": {kk: round(v, 1) for kk, v in peak.items()},
+        "diagnostics": {kk: round(v, 1) for kk, v in
+                        roofline_diagnostics_gups(head_path, head, sm_mhz, sms).items()},
         "avg_launch_ms": round(k["kernel_ms"] / max(k["launches"], 1), 4),
         "launches": k["launches"],
         "traffic": traffic,
@@ -701,6 +836,8 @@ def main():
         "gpu_launches_by_form": {kk: v["launches"] * 3 for kk, v in kernel.items()},
         "cpu_baseline": cpu,
         "paths": {kk: path_taken.get(kk) for kk in forms},
+        "brick_depth": {kk: depth_taken.get(kk) for kk in forms},
+        "sizes": sizes or None,
         "reciprocal_modes": rcp_modes,
         **extra,
     }

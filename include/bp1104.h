@@ -78,14 +78,18 @@ typedef enum {
      * every voxel still sums its projections in the same order. */
     BP_OPT_LANES_X = 4,
     /* Data path of the backprojection: 0 (default) automatic, 1 texture
-     * gathers, 2 TMA-staged shared-memory tiles.  With the same centring
-     * (BP_F16 / BP_BF16, or BP_OPT_BLOCK_CENTRE 0) the two give
-     * bit-identical volumes.  The automatic choice is the TMA path, the
-     * faster on GB300 for every storage type (most for BP_F32, whose 32-bit
-     * texture gathers the texture unit returns at half the 16-bit rate).
-     * The TMA path allocates two sets of 64 pair images on first use (1.2 GB
-     * for 1248x960 BP_F32, 0.6 GB for 16-bit storage).
-     * bp_query(BP_QUERY_LAST_PATH) reports the path taken. */
+     * gathers, 2 TMA-staged shared-memory tiles.  With per-projection
+     * centring (BP_OPT_BLOCK_CENTRE 0) the two give bit-identical BP_F32
+     * volumes; 16-bit storage differs between them by the rounding of the
+     * staged differences (the TMA path stores each pixel difference rounded
+     * once, the texture path differences the rounded pixels).  The automatic
+     * choice, made per batch, is the TMA path wherever the sampled
+     * footprints of its bricks fit its staged boxes (fine voxels: 512^3 and
+     * finer on the 1248x960 detector), else the texture path (coarse voxels,
+     * whose footprints are too wide to stage: 256^3 on that detector).  The
+     * TMA path allocates two sets of 64 staged images on first use (1.2 GB
+     * for a 1248x960 detector).  bp_query(BP_QUERY_LAST_PATH) reports the
+     * path taken. */
     BP_OPT_PATH = 5,
     /* 1 (default): skip, per block of voxels, the projections whose footprint
      * misses the detector (the line-wise clipping of Sect. 3.3 at block
@@ -105,7 +109,7 @@ typedef enum {
     /* 1 (default): centre the detector coordinates per block of voxels and
      * projection, 0: once per projection.  Applies to BP_F32 projections in
      * bp_add_projections (blocks: the texture kernel's thread block or the
-     * TMA path's 32x16x8 brick) and to bp_adjoint's shared-tile kernel
+     * TMA path's brick) and to bp_adjoint's shared-tile kernel
      * (32x32x4 blocks; BP_OPT_CULL 1).  Per-block centring costs a pre-pass
      * and 48 bytes of device memory per (block, projection of a batch), per
      * input set for bp_add_projections (768 MiB for a 512^3 volume on the
@@ -114,15 +118,29 @@ typedef enum {
      * footprint (rel-L2 5e-7 instead of 1e-5 for the backprojection on a
      * full 1248x960 detector, 6e-7 instead of 4e-6 for the adjoint).  16-bit
      * storage always centres per projection. */
-    BP_OPT_BLOCK_CENTRE = 8
+    BP_OPT_BLOCK_CENTRE = 8,
+    /* Depth of the TMA path's bricks of 32 x 16 x D voxels: 0 (default)
+     * automatic, or D = 8, 12, 16.  Deeper bricks give each thread more
+     * voxels per staged projection (less per-projection work per update) but
+     * need taller staged boxes; the automatic choice takes, per batch, the
+     * deepest brick whose box holds the footprints of a sample of bricks
+     * (16 for 512^3 and 1024^3 on a 1248x960 detector).  With
+     * per-projection centring (16-bit storage, or BP_OPT_BLOCK_CENTRE 0)
+     * the depth changes speed only: every voxel sums the same float32 terms
+     * in the same order.  With per-brick centring (the BP_F32 default) the
+     * centring offsets follow the brick, so the float32 rounding differs
+     * between depths within the same accuracy.
+     * bp_query(BP_QUERY_LAST_BRICK_DEPTH) reports the depth used. */
+    BP_OPT_BRICK_DEPTH = 9
 } bp_option;
 
 /* Queries for bp_query. */
 typedef enum {
     BP_QUERY_LAST_PATH = 1,          /* data path of the last batch: 1 texture, 2 TMA, 0 none yet */
     BP_QUERY_PROJECTIONS_ADDED = 2,  /* projections accumulated since create / reset / set_state */
-    BP_QUERY_UPDATES_COMPUTED = 3    /* voxel updates actually computed since create (culled blocks
+    BP_QUERY_UPDATES_COMPUTED = 3,   /* voxel updates actually computed since create (culled blocks
                                       * excluded; synchronises the stream) */
+    BP_QUERY_LAST_BRICK_DEPTH = 4    /* brick depth of the last TMA-path batch (8, 12, 16; 0 none yet) */
 } bp_query_what;
 
 /* ---------------------------------------------------------------- context */
@@ -318,10 +336,12 @@ bp_status bp_row_filter_bwd(long long rows, int isx, int T, const float *h, cons
  * owns the device.  Its scratch is a fixed 128 KiB device array inside the
  * library (256 blocks x 128 taps of float32), held by every GPU that loads
  * the library until the process exits; T above 128 is rejected with
- * BP_EINVAL.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (e.g. on
- * two streams) race and must be serialised by the caller.  Makes no call to
+ * BP_EINVAL.  The first call in each CUDA context (the device's primary
+ * context, a context created after cudaDeviceReset, or a non-primary
+ * context made current by the caller) looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (e.g. on two
+ * streams) race and must be serialised by the caller.  Makes no call to
  * cudaMalloc, cudaMallocAsync or cudaFree. */
 bp_status bp_row_filter_bwd_noalloc(long long rows, int isx, int T, const float *h,
                                     const float *in, const float *g, float *gin, float *gh,

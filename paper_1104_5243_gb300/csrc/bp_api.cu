@@ -8,6 +8,7 @@
 // backprojects the other; events order the two streams, so the compute
 // stream never reads a set before its copy finished and the copy stream
 // never overwrites a set the compute stream still reads.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -71,11 +72,15 @@ struct bp_ctx {
     std::vector<cudaEvent_t> ev;   // start/stop pairs, reused
     int path = 0;                  // BP_OPT_PATH: 0 auto, 1 texture, 2 TMA
     int last_path = 0;             // path of the last batch (1 or 2)
-    // TMA path: pair images per set (kMaxBatch slots each) and their maps
+    // TMA path: staged images per set (kMaxBatch slots each) and their
+    // tensor maps, one set of maps per brick depth (the box height differs)
     void *pairs[2] = {nullptr, nullptr};
-    size_t pair_pitch = 0;         // pair elements per row
+    size_t pair_pitch = 0;         // 8-byte elements per row
     size_t pair_slot_bytes = 0;
-    CUtensorMap maps[2][kMaxBatch];
+    CUtensorMap maps[3][2][kMaxBatch];
+    bool maps_ready[3] = {false, false, false};
+    int brick_depth = 0;           // BP_OPT_BRICK_DEPTH (0 automatic)
+    int last_depth = 0;            // brick depth of the last TMA batch
     int *err_dev = nullptr;        // set by a kernel whose bounded wait gave up
     bool cull = true;              // BP_OPT_CULL
     bool host_direct = true;       // BP_OPT_HOST_DIRECT (f32 host images: copy engine into arrays)
@@ -349,6 +354,11 @@ extern "C" bp_status bp_set_option(bp_ctx *c, int option, long long value)
             return fail(c, BP_EINVAL, "bp_set_option: TIMING takes 0 or 1");
         c->timing = value != 0;
         return BP_OK;
+    case BP_OPT_BRICK_DEPTH:
+        if (value != 0 && value != 8 && value != 12 && value != 16)
+            return fail(c, BP_EINVAL, "bp_set_option: BRICK_DEPTH takes 0 (automatic), 8, 12 or 16");
+        c->brick_depth = (int)value;
+        return BP_OK;
     default:
         return fail(c, BP_EINVAL, "bp_set_option: unknown option %d", option);
     }
@@ -423,42 +433,123 @@ static VolGeom vol_geom(const bp_ctx *c)
 
 static int pair_kind(const bp_ctx *c)
 {
-    return c->dtype == BP_F32 ? kPairF32 : c->dtype == BP_F16 ? kPairF16 : kPairBF16;
+    return c->dtype == BP_F32 ? kPairF32 : c->dtype == BP_F16 ? kQuadF16 : kQuadBF16;
 }
 
-// Pair images for the TMA path: allocated on first use, with one tensor map
-// per slot (the slots' addresses never change).
+// Staged images for the TMA path (float32 pair images or 16-bit column
+// quads, 8-byte elements), allocated on first use; the slots' addresses
+// never change.
 static bp_status ensure_pairs(bp_ctx *c)
 {
     if (c->pairs[0] != nullptr)
         return BP_OK;
-    EncodeTiledFn enc = encode_tiled();
-    if (enc == nullptr)
+    if (encode_tiled() == nullptr)
         return fail(c, BP_ECUDA, "TMA path: cuTensorMapEncodeTiled is not available from the driver");
-    const int kind = pair_kind(c);
-    const size_t pair_bytes = kind == kPairF32 ? 8 : 4;
-    const size_t align = kind == kPairF32 ? 2 : 4;               // pairs per 16 bytes
-    const size_t width = (size_t)c->isx + 1;                     // pair columns 0 .. isx
-    c->pair_pitch = (width + align - 1) / align * align;
-    c->pair_slot_bytes = c->pair_pitch * pair_bytes * c->isy;
-    const size_t words = pair_bytes / 4;
-    for (int s = 0; s < 2; ++s) {
+    const size_t width = (size_t)c->isx + 1;                     // element columns 0 .. isx
+    c->pair_pitch = (width + kTmaAlign - 1) / kTmaAlign * kTmaAlign;
+    c->pair_slot_bytes = c->pair_pitch * 8 * (size_t)tma_image_rows(pair_kind(c), c->isy);
+    for (int s = 0; s < 2; ++s)
         CTX_CK(c, cudaMalloc(&c->pairs[s], c->pair_slot_bytes * kMaxBatch));
+    return BP_OK;
+}
+
+static int depth_index(int zpl) { return zpl == 4 ? 0 : zpl == 6 ? 1 : 2; }
+
+// One tensor map per slot for the box of brick depth 2 zpl (two 32-bit
+// words per element; rows of the staged image).
+static bp_status ensure_maps(bp_ctx *c, int zpl)
+{
+    const int di = depth_index(zpl);
+    if (c->maps_ready[di])
+        return BP_OK;
+    EncodeTiledFn enc = encode_tiled();
+    const int kind = pair_kind(c);
+    const size_t width = (size_t)c->isx + 1;
+    for (int s = 0; s < 2; ++s) {
         for (int j = 0; j < kMaxBatch; ++j) {
             void *base = static_cast<char *>(c->pairs[s]) + c->pair_slot_bytes * j;
-            const cuuint64_t dims[2] = {width * words, (cuuint64_t)c->isy};
-            const cuuint64_t strides[1] = {c->pair_pitch * pair_bytes};
-            const cuuint32_t box[2] = {(cuuint32_t)((kind == kPairF32 ? TmaBox<kPairF32>::BU : TmaBox<kPairF16>::BU) * words),
-                                       (cuuint32_t)(kind == kPairF32 ? TmaBox<kPairF32>::BV : TmaBox<kPairF16>::BV)};
+            const cuuint64_t dims[2] = {width * 2, (cuuint64_t)tma_image_rows(kind, c->isy)};
+            const cuuint64_t strides[1] = {c->pair_pitch * 8};
+            const cuuint32_t box[2] = {(cuuint32_t)(kTmaBU * 2), (cuuint32_t)tma_rows(zpl, kind != kPairF32)};
             const cuuint32_t estr[2] = {1, 1};
-            CUresult r = enc(&c->maps[s][j], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, base, dims, strides, box, estr,
+            CUresult r = enc(&c->maps[di][s][j], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, base, dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS)
                 return fail(c, BP_ECUDA, "TMA path: cuTensorMapEncodeTiled failed (%d)", (int)r);
         }
     }
+    c->maps_ready[di] = true;
     return BP_OK;
+}
+
+// Host model of the pre-pass's box rule on a sample of bricks (a 5 x 5 x 5
+// grid of brick positions spanning the volume) and up to 16 projections of
+// the batch, in float64: of the sampled (brick, projection) pairs whose
+// footprint reaches the detector, the fraction whose box fits kTmaBU
+// element columns by bv rows (pair-image rule: rows floor(v) - 1 ..
+// floor(v_max) + 2) for bricks 32 x 16 x bz; 1 if no sampled pair is
+// visible.
+static double box_fit_fraction(const bp_ctx *c, const double *A, int m, int bz, int bv)
+{
+    const int nb[3] = {(c->L + kBrickX - 1) / kBrickX, (c->L + kBrickY - 1) / kBrickY, (c->Lz + bz - 1) / bz};
+    const int ext[3] = {kBrickX, kBrickY, bz}, lim[3] = {c->L, c->L, c->Lz};
+    constexpr int K = 5;
+    long vis = 0, fit = 0;
+    const int pstep = m > 16 ? m / 16 : 1;
+    for (int p = 0; p < m; p += pstep) {
+        const double *a = A + 12 * (size_t)p;
+        for (int q = 0; q < K * K * K; ++q) {
+            int lo[3], hi[3];
+            for (int d = 0, qq = q; d < 3; ++d, qq /= K) {
+                const int bi = (int)std::lround((double)(qq % K) * (nb[d] - 1) / (K - 1));
+                lo[d] = bi * ext[d];
+                hi[d] = std::min(lo[d] + ext[d], lim[d]) - 1;
+            }
+            double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+            for (int cn = 0; cn < 8; ++cn) {
+                const double X = c->O[0] + c->R * ((cn & 1) ? hi[0] : lo[0]);
+                const double Y = c->O[1] + c->R * ((cn & 2) ? hi[1] : lo[1]);
+                const double Z = c->O[2] + c->R * ((cn & 4) ? hi[2] : lo[2]);
+                const double w = a[8] * X + a[9] * Y + a[10] * Z + a[11];
+                const double u = (a[0] * X + a[1] * Y + a[2] * Z + a[3]) / w;
+                const double v = (a[4] * X + a[5] * Y + a[6] * Z + a[7]) / w;
+                umin = std::fmin(umin, u), umax = std::fmax(umax, u);
+                vmin = std::fmin(vmin, v), vmax = std::fmax(vmax, v);
+            }
+            const double cmin = std::floor(umin), cmax = std::floor(umax) + 2;
+            const double rmin = std::floor(vmin) - 1, rmax = std::floor(vmax) + 2;
+            if (cmax < 0 || cmin > c->isx || rmax < 0 || rmin > c->isy - 1)
+                continue;
+            ++vis;
+            const double cx0 = std::floor(cmin / kTmaAlign) * kTmaAlign;
+            if (cmax - cx0 + 1 <= kTmaBU && rmax - rmin + 1 <= bv)
+                ++fit;
+        }
+    }
+    return vis ? (double)fit / (double)vis : 1.0;
+}
+
+// Data path and brick depth of a batch.  Forced depths and the forced TMA
+// path take the caller's choice; otherwise 16-deep bricks when their box
+// holds the sampled footprints of 99 % of the visible pairs (the rest take
+// the slower global-memory branch), else 8-deep bricks, and the texture path
+// when even the 8-deep box holds fewer than 90 % of them (coarse voxels).
+// Measured on GB300 at 512^3 x 496 x 1248x960 (GUP/s per step for depths
+// 8 / 12 / 16): f32 1403 / 1379 / 1413, f16 1511 / 1497 / 1536; so 12 is
+// never the automatic choice.
+static void choose_path(const bp_ctx *c, const double *A, int m, bool *tma, int *zpl)
+{
+    *zpl = c->brick_depth ? c->brick_depth / 2 : 4;
+    *tma = c->path != 1;
+    if (c->path == 1 || c->brick_depth)
+        return;
+    if (box_fit_fraction(c, A, m, 16, tma_rows(8, false)) >= 0.99) {
+        *zpl = 8;
+        return;
+    }
+    if (c->path == 0 && box_fit_fraction(c, A, m, 8, tma_rows(4, false)) < 0.9)
+        *tma = false;
 }
 
 static bp_status record_start(bp_ctx *c, cudaEvent_t *stop)
@@ -504,12 +595,18 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
     for (int c0 = 0; c0 < n; c0 += c->batch) {
         const int m = n - c0 < c->batch ? n - c0 : c->batch;
         const double *A0 = A + 12 * (size_t)c0;
-        // Automatic choice, by measurement on GB300 (512^3 x 1248x960): the
-        // TMA path for every storage type (f32 1313 against 801 GUP/s: the
-        // texture unit's data return bounds 32-bit gathers; bf16 1249
-        // against 1198; f16 1220-1270 against 1240).
-        const bool tma = c->path != 1;
+        // Automatic choice, by measurement on GB300: the TMA path wherever its
+        // boxes hold the bricks' footprints (512^3 x 1248x960: f32 1388
+        // against 796 GUP/s on the texture path, whose 32-bit gathers the
+        // texture unit returns at half the 16-bit rate), the texture path for
+        // coarse voxels (256^3 on that detector: 593 against 468 GUP/s for
+        // the TMA path's global-memory branch).
+        bool tma = true;
+        int zpl = 4;
+        choose_path(c, A0, m, &tma, &zpl);
         st = tma ? ensure_pairs(c) : ensure_arrays(c);
+        if (st == BP_OK && tma)
+            st = ensure_maps(c, zpl);
         if (st != BP_OK)
             return st;
         const int s = c->next_set;
@@ -559,7 +656,7 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
         FwdBatch b;
         unsigned long long *masks = nullptr;
         float4 *centres = nullptr;
-        int tile[3] = {kBrickX, kBrickY, kBrickZ};
+        int tile[3] = {kBrickX, kBrickY, 2 * zpl};
         if (!tma)
             fwd_tile(c->lanes_x, &tile[0], &tile[1], &tile[2]);
         const long long nb = tile_count(c->L, c->Lz, tile[0], tile[1], tile[2]);
@@ -620,9 +717,8 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
                     c->box_bricks[s] = nb;
                 }
                 boxes = c->boxes[s];
-                const int kind = pair_kind(c);
-                bs = kind == kPairF32 ? BoxSpec{TmaBox<kPairF32>::BU, TmaBox<kPairF32>::BV, kPairAlign<kPairF32>}
-                                      : BoxSpec{TmaBox<kPairF16>::BU, TmaBox<kPairF16>::BV, kPairAlign<kPairF16>};
+                const bool quad = pair_kind(c) != kPairF32;
+                bs = BoxSpec{kTmaBU, tma_rows(zpl, quad), kTmaAlign, quad ? 1 : 0};
             }
             CTX_CK(c, launch_block_prepass(b, centres ? &cb : nullptr, g, c->isx, c->isy, tile[0], tile[1], tile[2],
                                            masks, centres, boxes ? &bs : nullptr, boxes,
@@ -648,13 +744,15 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
                 tb.m[j][1] = row4(a, 1, 1.0 - kv);
                 tb.m[j][2] = row4(a, 2, 0.0);
                 tb.k[j] = make_int2((int)ku, (int)kv);
-                tb.map[j] = c->maps[s][j];
+                tb.map[j] = c->maps[depth_index(zpl)][s][j];
                 tb.img[j] = static_cast<const char *>(c->pairs[s]) + c->pair_slot_bytes * j;
             }
             tb.centres = centres;
             tb.boxes = c->boxes[s];
             tb.bricks = nb;
             tb.final_out = c0 + m == n ? final_out : nullptr;
+            tb.zpl = zpl;
+            tb.vec4 = c->L % 4 == 0 && (tb.final_out == nullptr || reinterpret_cast<uintptr_t>(tb.final_out) % 16 == 0);
             CTX_CK(c, launch_bp_tma(tb, c->vol, g, pair_kind(c), !c->vol_zero, c->ieee_rcp, c->err_dev, c->work_dev,
                                     c->stream));
         } else {
@@ -664,6 +762,8 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
         if (ev_stop)
             CTX_CK(c, cudaEventRecord(ev_stop, c->stream));
         c->last_path = tma ? 2 : 1;
+        if (tma)
+            c->last_depth = 2 * zpl;
         c->vol_zero = false;
         CTX_CK(c, cudaEventRecord(c->kern_done[s], c->stream));
     }
@@ -701,6 +801,9 @@ extern "C" bp_status bp_query(bp_ctx *c, int what, long long *value)
         return BP_OK;
     case BP_QUERY_PROJECTIONS_ADDED:
         *value = c->n_added;
+        return BP_OK;
+    case BP_QUERY_LAST_BRICK_DEPTH:
+        *value = c->last_depth;
         return BP_OK;
     case BP_QUERY_UPDATES_COMPUTED: {
         unsigned long long dev = 0;

@@ -329,11 +329,14 @@ __device__ BlockRec block_centre(const FwdBatch &b, const CentreBatch &cb, int i
     return rec;
 }
 
-// TMA-path box decision of one (brick, projection): the pair columns and
-// image rows the brick's corner projections touch, with a pixel of margin
-// (pair column = floor(u') + ku; top row = floor(v') + kv - 1), decide
-// between culling, one staged box, and the global-memory path.  kb are the
-// offsets the kernel's floor(u'), floor(v') are relative to.
+// TMA-path box decision of one (brick, projection): the element columns
+// and rows the brick's corner projections touch, with a pixel of margin,
+// decide between culling, one staged box, and the global-memory path.  An
+// update at pixel (iu, iv) reads element column iu + 1 = floor(u') + ku, and
+// row iv = floor(v') + kv - 1 (pair images: rows iv and iv + 1) or stored row
+// iv + 1 (column quads, whose element at stored row k + 1 carries image rows
+// k and k + 1).  kb are the offsets the kernel's floor(u'), floor(v') are
+// relative to.
 __device__ int4 tma_box(const FwdBatch &b, int i, const VolGeom &g, int isx, int isy, int x0, int y0, int z0,
                         int x1, int y1, int z1, int2 kb, const BoxSpec &bs)
 {
@@ -359,16 +362,19 @@ __device__ int4 tma_box(const FwdBatch &b, int i, const VolGeom &g, int isx, int
     vmin = fminf(fmaxf(vmin, -1.0e6f), 1.0e6f);
     vmax = fminf(fmaxf(vmax, -1.0e6f), 1.0e6f);
     const int ku = (int)b.k[i].x, kv = (int)b.k[i].y;
+    // stored row of the update's (top) element: floor(v') + kv - 1 + quad
+    const int rs = bs.quad ? 0 : -1;
     const int cmin = (int)floorf(umin) + ku - 1, cmax = (int)floorf(umax) + ku + 1;
-    const int rmin = (int)floorf(vmin) + kv - 2, rmax = (int)floorf(vmax) + kv + 1;
-    if (cmax < 0 || cmin > isx || rmax < 0 || rmin > isy - 1)
+    const int rmin = (int)floorf(vmin) + kv + rs - 1, rmax = (int)floorf(vmax) + kv + rs + (bs.quad ? 1 : 2);
+    const int rows = bs.quad ? isy + 1 : isy;   // stored rows of the image
+    if (cmax < 0 || cmin > isx || rmax < 0 || rmin > rows - 1)
         return make_int4(0, 0, 0, 0);   // nothing of this brick lands on the detector
     const int cx0 = cmin & ~(bs.align - 1), ry0 = rmin;
     if (cmax < cx0 + bs.bu && rmax < ry0 + bs.bv) {
-        const int cu = kb.x - cx0, cv = kb.y - 1 - ry0;
+        const int cu = kb.x - cx0, cv = kb.y + rs - ry0;
         return make_int4(1, __float_as_int((float)(cv * bs.bu + cu) + 12582912.0f), cx0, ry0);
     }
-    return make_int4(2, kb.x, kb.y - 1, 0);
+    return make_int4(2, kb.x, kb.y + rs, 0);
 }
 
 // One thread per tile (the texture kernel's block or the TMA path's brick),

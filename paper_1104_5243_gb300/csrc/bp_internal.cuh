@@ -36,26 +36,41 @@ struct FwdBatch {
     int n;
 };
 
+// Four values of the scalar type T: float4 for float, a plain aggregate for
+// double (the direct kernels are templates on T; the float64 instantiation
+// serves gradient checks only).
+struct Dbl4 {
+    double x, y, z, w;
+};
+template <typename T> struct Vec4Of;
+template <> struct Vec4Of<float> { using type = float4; };
+template <> struct Vec4Of<double> { using type = Dbl4; };
+template <typename T> using Vec4 = typename Vec4Of<T>::type;
+
 // Same for the adjoint: centred matrix rows (row_u - ku row_w), the offsets
 // as integers, and the output image offset.
-struct AdjBatch {
-    float4 m[kMaxBatch][3];
+template <typename T>
+struct AdjBatchT {
+    Vec4<T> m[kMaxBatch][3];
     int2 k[kMaxBatch];
     long long out_off[kMaxBatch];
     const float4 *centres;   // per-block centring records (shared-tile kernel; NULL: per projection)
     long long blocks;        // blocks of the volume (record plane stride)
     int n;
 };
+using AdjBatch = AdjBatchT<float>;
 // The shared-tile adjoint kernel's block of voxels (the pre-pass tile for
 // its centring records).
 constexpr int kAdjBlockX = 32, kAdjBlockY = 32, kAdjBlockZ = 4;
 
 // Volume: L x L x Lz voxels (x fastest; Lz = L for a cube, Lz < L for a
 // z-slab of an L^3 grid), voxel size R, centre of voxel (0,0,0) at O.
-struct VolGeom {
+template <typename T>
+struct VolGeomT {
     int L, Lz;
-    float R, Ox, Oy, Oz;
+    T R, Ox, Oy, Oz;
 };
+using VolGeom = VolGeomT<float>;
 
 // Texture storage kinds: float channel (FP32 or FP16 arrays; the texture
 // unit widens FP16 exactly) or raw 16-bit words holding BF16.
@@ -120,7 +135,8 @@ long long tile_count(int L, int Lz, int tx, int ty, int tz);
 // The offsets are relative to the brick's centring offsets with per-brick
 // centring, else to the projection's.
 struct BoxSpec {
-    int bu, bv, align;   // box columns and rows (pairs), column alignment (pairs)
+    int bu, bv, align;   // box columns and rows (elements), column alignment (elements)
+    int quad;            // column quads: an element carries rows k and k + 1, stored at row k + 1
 };
 cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const VolGeom &g, int isx, int isy,
                                  int tx, int ty, int tz, unsigned long long *masks, float4 *centres,
@@ -133,44 +149,54 @@ cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom
                               float *out, int isx, int isy, bool ieee_rcp, bool smem, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
-// TMA / shared-memory path (bp_tma.cu).  Bricks of 32 x 16 x 8 voxels per
-// block of 256 consumer threads (16 voxels each) and one producer warp;
-// projections staged as "pair images" (element c of a row holds pixels c-1
-// and c; for float32, pixel c-1 and the difference of c and c-1) and loaded
-// per brick and projection as one TMA box of BU pair
-// columns by BV rows.  A box of that size holds the footprint of 99.9 % of
-// the visible (brick, projection) pairs of the 512^3 C-arm scan (97 % with
-// 32 rows); larger footprints (bricks near the source) read the pair image
-// from global memory.
-constexpr int kBrickX = 32, kBrickY = 16, kBrickZ = 8;
-enum PairKind { kPairF32 = 0, kPairF16 = 1, kPairBF16 = 2 };
-template <int KIND> struct TmaBox;
-// Row pitches of 228 words (f32 pairs) and 100 words (16-bit pairs), both
-// 4 modulo 32, put successive box rows 4 banks apart, so lanes on the same
-// column in different rows do not conflict.
-template <> struct TmaBox<kPairF32> { static constexpr int BU = 114, BV = 36, S = 2; };
-template <> struct TmaBox<kPairF16> { static constexpr int BU = 100, BV = 36, S = 3; };
-template <> struct TmaBox<kPairBF16> { static constexpr int BU = 100, BV = 36, S = 3; };
-// 32-bit words per pair, and the pair-column alignment that keeps the TMA
-// box origin on a 16-byte boundary.
-template <int KIND> constexpr int kPairWords = KIND == kPairF32 ? 2 : 1;
-template <int KIND> constexpr int kPairAlign = KIND == kPairF32 ? 2 : 4;
+// TMA / shared-memory path (bp_tma.cu).  Bricks of 32 x 16 x (2 ZPL) voxels
+// per block of 256 consumer threads (4 ZPL voxels each) and one producer
+// warp; projections staged as images of 8-byte elements, loaded per brick
+// and projection as one TMA box of BU element columns by BV rows:
+//   * float32 "pair images": element c of row k holds (p[k][c-1],
+//     p[k][c] - p[k][c-1]); an update reads two elements (rows iv, iv+1);
+//   * 16-bit "column quads": element c of stored row j (image row k = j - 1)
+//     holds the 16-bit pairs (p[k][c-1], p[k+1][c-1]) and (p[k][c] -
+//     p[k][c-1], p[k+1][c] - p[k+1][c-1]), the differences taken in float32
+//     and rounded once; an update reads one element and interpolates both
+//     rows along u with one packed two-lane FMA.
+// ZPL (voxels per lane along z) sets the brick depth: 4, 6 or 8 (8-, 12-
+// and 16-deep bricks).  Deeper bricks spread the per-projection work of a
+// thread over more updates but need taller boxes; the host picks, per
+// batch, the deepest brick whose box holds the sampled footprints.  The box
+// heights come from a CPU model of the pre-pass's box rule over the 512^3
+// C-arm scan: 36 rows hold 99.7 % of the visible 8-deep footprints, 48 rows
+// 99.7 % of the 12-deep ones and 61 rows 99.8 % of the 16-deep ones (114
+// element columns hold 99.99 %); larger footprints (bricks near the
+// source) read the image from global memory.
+constexpr int kBrickX = 32, kBrickY = 16;
+enum PairKind { kPairF32 = 0, kQuadF16 = 1, kQuadBF16 = 2 };
+constexpr int kTmaBU = 114;   // element columns: a row pitch of 228 words, 4 modulo 32 (rows 4 banks apart)
+constexpr int kTmaAlign = 2;  // element-column alignment that keeps the box origin on 16 bytes
+// Box rows of the float32 pair images per ZPL; a column-quad box is one row
+// shorter (each element carries the row below).
+__host__ __device__ constexpr int tma_rows(int zpl, bool quad)
+{
+    return (zpl == 4 ? 36 : zpl == 6 ? 48 : 61) - (quad ? 1 : 0);
+}
+constexpr int kTmaStages = 2;
 constexpr int kTmaWaitIters = 1 << 14;          // bounded waits: at most ~2 s
 constexpr unsigned kTmaSuspendNs = 100000;        // suspend hint per try, ns
-constexpr int kTmaMaxStages = 3;                  // deepest shared-memory ring (S above)
 
 struct TmaBatch {
-    CUtensorMap map[kMaxBatch];        // one per projection's pair image
+    CUtensorMap map[kMaxBatch];        // one per projection's image (box of this batch's ZPL)
     float4 m[kMaxBatch][3];            // rows as in FwdBatch (centred, +1 folded)
     int2 k[kMaxBatch];                 // integer centring offsets (ku, kv)
-    const void *img[kMaxBatch];        // pair image base, for the global path
+    const void *img[kMaxBatch];        // image base, for the global path
     const float4 *centres;             // per-brick centring records (NULL: per projection)
     const int4 *boxes;                 // per-(brick, projection) box decisions (pre-pass)
     long long bricks;                  // bricks of the volume (record plane stride)
     float *final_out;                  // NULL, or a second destination of the updated volume
                                        // (device-addressable, same layout): the finished
                                        // volume written by the last batch's launch
-    int n, isx, isy, pitch;            // pitch: pair elements per row
+    int n, isx, isy, pitch;            // pitch: elements per row
+    int zpl;                           // voxels per lane along z (4, 6, 8)
+    int vec4;                          // volume (and final_out) rows 16-byte aligned: float4 I/O
 };
 
 cudaError_t launch_bp_tma(const TmaBatch &b, float *vol, const VolGeom &g, int pair_kind, bool accumulate,
@@ -181,6 +207,9 @@ struct PairBatch {
     void *dst[kMaxBatch];
     int n;
 };
+// Images of the TMA path: rows() of them per projection (isy for pair
+// images, isy + 1 for column quads).
+__host__ __device__ constexpr int tma_image_rows(int pair_kind, int isy) { return pair_kind == kPairF32 ? isy : isy + 1; }
 cudaError_t launch_pair_images(const PairBatch &b, int isx, int isy, int pitch, int pair_kind, cudaStream_t s);
 
 // Copy (mode 0) or FP16 (1) / BF16 (2) conversion of up to kMaxBatch FP32

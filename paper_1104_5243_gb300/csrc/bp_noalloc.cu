@@ -9,11 +9,14 @@
 // gradients with its scratch in a fixed, file-scope device array instead.
 //
 // The scratch (kNoAllocBlocks x kNoAllocTaps floats, 128 KiB) lives in every
-// GPU that loads the library until the process exits.  Its device address is
-// looked up once per device with cudaGetSymbolAddress, on the first call made
-// with that device current.  All calls share the array, so calls whose work
-// overlaps on the GPU (for example on two streams) race on it and must be
-// serialised by the caller.
+// GPU that loads the library until the process exits.  In host code the
+// array's name only stands for the device symbol, so its device address is
+// looked up with cudaGetSymbolAddress: once per CUDA context (keyed by the
+// context's unique ID, so a context created after cudaDeviceReset, or a
+// non-primary context, gets its own lookup), on the first call made in that
+// context.  All calls share the array, so calls whose work overlaps on the
+// GPU (for example on two streams) race on it and must be serialised by the
+// caller.
 #include <mutex>
 
 #include "bp_internal.cuh"
@@ -23,7 +26,7 @@ namespace bp {
 constexpr int kNoAllocTaps = 128;      // largest filter the scratch serves
 constexpr int kNoAllocBlocks = 256;    // persistent grid, one scratch row each
 constexpr int kNoAllocRows = 4;        // rows per work item
-constexpr int kNoAllocMaxDevices = 64;
+constexpr int kNoAllocMaxContexts = 64;
 
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocBlocks * kNoAllocTaps];
 
@@ -74,12 +77,18 @@ row_filter_bwd_noalloc_kernel(long long rows, int isx, int T, const float *__res
             }
         }
         if (partial != nullptr && grp < ngrp) {
+            // the group's terms summed on their own, then added to the
+            // block's running sum once: the running sum then takes one term
+            // per row group instead of one per product, which keeps its
+            // float32 rounding at the level of the regular kernel's
+            float part = 0.f;
             for (int rr = 0; rr < kNoAllocRows; ++rr) {
                 const float *xr = xs + rr * pitch + T + tap - T / 2;    // xr[j] = in[j + tap - T/2]
                 const float *gr = gs + rr * pitch + T;
                 for (int j = grp; j < isx; j += ngrp)
-                    acc = fmaf(gr[j], xr[j], acc);
+                    part = fmaf(gr[j], xr[j], part);
             }
+            acc += part;
         }
     }
     if (partial == nullptr)
@@ -114,28 +123,71 @@ reduce_noalloc_kernel(int nblk, int T, const float *__restrict__ partial, float 
         gh[t] = red[0];
 }
 
-// Device address of g_noalloc_scratch for the current device, looked up once
-// per device.  In host code the array's name only stands for the device
-// symbol; only the address returned here may be handed to a kernel.
+// Device address of g_noalloc_scratch in the current context, looked up
+// once per context.  In host code the array's name only stands for the
+// device symbol; only the address returned here may be handed to a kernel.
+// The context is identified by cuCtxGetId (unique over the process's life,
+// unlike a context handle or a device ordinal, which a context created after
+// cudaDeviceReset may reuse), taken from the driver through the runtime's
+// entry-point query.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+static cudaError_t current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+    });
+    if (get_current == nullptr || get_id == nullptr)
+        return cudaErrorNotSupported;
+    // make the device's primary context current if the thread has none yet
+    cudaError_t e = cudaFree(nullptr);
+    if (e != cudaSuccess)
+        return e;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, id) != CUDA_SUCCESS)
+        return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
+
 static cudaError_t noalloc_scratch(float **out)
 {
     static std::mutex mu;
-    static float *addr[kNoAllocMaxDevices] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static unsigned long long ids[kNoAllocMaxContexts] = {};
+    static float *addr[kNoAllocMaxContexts] = {};
+    static int used = 0;
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
     if (e != cudaSuccess)
         return e;
-    if (dev < 0 || dev >= kNoAllocMaxDevices)
-        return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
-    if (addr[dev] == nullptr) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess)
-            return e;
-        addr[dev] = static_cast<float *>(p);
+    for (int q = 0; q < used; ++q) {
+        if (ids[q] == id) {
+            *out = addr[q];
+            return cudaSuccess;
+        }
     }
-    *out = addr[dev];
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+        return e;
+    // the table keeps the most recent contexts; a context dropped from it
+    // is looked up again on its next call
+    const int slot = used < kNoAllocMaxContexts ? used++ : (int)(id % kNoAllocMaxContexts);
+    ids[slot] = id;
+    addr[slot] = static_cast<float *>(p);
+    *out = addr[slot];
     return cudaSuccess;
 }
 

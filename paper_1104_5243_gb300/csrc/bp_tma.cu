@@ -1,16 +1,16 @@
 // Backprojection with projections staged through TMA into shared memory
-// (Sect. 3.1, Listing 1; the same arithmetic as bp_fwd.cu, different data
+// (Sect. 3.1, Listing 1; the same geometry as bp_fwd.cu, different data
 // path).
 //
 // Why: the texture unit returns 2x2 gathers of 32-bit texels at half the
 // rate of 16-bit ones, which bounds the float32 form of the texture kernel.
-// Here each block owns a 32 x 16 x 8 voxel brick.  For every projection the
-// per-tile pre-pass (bp_fwd.cu) has projected the brick's 8 corners and
-// decided to
+// Here each block owns a 32 x 16 x (2 ZPL) voxel brick.  For every
+// projection the per-tile pre-pass (bp_fwd.cu) has projected the brick's 8
+// corners and decided to
 //   * cull the projection when the footprint misses the detector (every
 //     term is then exactly zero -- the line-wise clipping of Sect. 3.3 at
 //     brick granularity), or
-//   * load the footprint box of the projection's "pair image" with one
+//   * load the footprint box of the projection's staged image with one
 //     cp.async.bulk.tensor.2d into a stage of a shared-memory ring,
 //     completing on an mbarrier; out-of-range rows/columns are zero-filled
 //     by the TMA unit, which is the zero padding of Sect. 3.3, or
@@ -19,15 +19,26 @@
 // The block stages those decisions; one producer lane issues the copies of
 // the projections the brick computes, and the consumers skip culled ones
 // without touching the ring.
-// The pair image stores element c = (p[c-1], p[c]) of each row (zero outside
-// the detector), so the four corners of an update are two shared-memory
-// loads: (tl, tr) from row iv and (bl, br) from row iv+1.  Float32 pairs
-// hold (p[c-1], p[c] - p[c-1]) instead: the difference is the float32
-// subtraction the horizontal interpolation needs anyway (the texture kernel
-// computes the same one), done once per pixel instead of once per update.
 //
-// The coordinates, fractions and interpolation are computed exactly as in
-// the texture kernel, so both paths give bit-identical volumes.
+// Staged images hold 8-byte elements, so that the four corners of an update
+// come from one or two shared-memory loads:
+//   * float32 pair images: element c of row k = (p[k][c-1], p[k][c] -
+//     p[k][c-1]); an update loads row iv and row iv + 1, and the difference
+//     is the float32 subtraction the horizontal interpolation needs anyway,
+//     done once per pixel instead of once per update;
+//   * 16-bit column quads: element c of stored row k + 1 = the 16-bit pairs
+//     (p[k][c-1], p[k+1][c-1]) and (p[k][c] - p[k][c-1], p[k+1][c] -
+//     p[k+1][c-1]); an update loads one element, interpolates both rows
+//     along u with one packed two-lane FMA (fraction rounded to the storage
+//     type), and interpolates along v in float32.
+// Coordinates, the weight 1/w^2 and the accumulation are float32 in every
+// form (Sect. 3.1's single precision; the 16-bit forms only store the
+// projections in 16 bits).
+//
+// Each thread accumulates its 4 ZPL voxels over the whole batch in
+// registers; at the end the block stages its sums in shared memory and
+// updates the volume with float4 loads and stores (coalesced rows of 32
+// voxels), so the volume crosses HBM once per batch.
 //
 // Every wait on an mbarrier is bounded; on timeout the block records an
 // error flag the host turns into BP_ETIMEOUT, the producer waits (bounded)
@@ -68,6 +79,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // try_wait with a suspend-time hint: a waiting warp sleeps (for at most
 // the hint) until the phase completes instead of spinning on issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
@@ -100,6 +116,12 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Barrier of the 256 consumer threads only (the producer warp has left).
+__device__ __forceinline__ void consumers_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+}
+
 // Integer value of an integer-valued float with |f| < 2^22, without the
 // float-to-int conversion unit: adding 1.5 * 2^23 puts the integer in the
 // low mantissa bits.
@@ -110,113 +132,106 @@ __device__ __forceinline__ int int_of_integral(float f)
     return __float_as_int(f + kIntMagic) - (int)kIntMagicBits;
 }
 
-// Shared-memory loads at a 32-bit shared address plus a constant offset.
+// 8-byte shared-memory load at a 32-bit shared address plus a constant.
 template <int OFF>
-__device__ __forceinline__ float2 lds_f2(uint32_t a)
+__device__ __forceinline__ uint2 lds_u2(uint32_t a)
 {
-    float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(a), "n"(OFF));
-    return v;
-}
-template <int OFF>
-__device__ __forceinline__ unsigned int lds_u32(uint32_t a)
-{
-    unsigned int v;
-    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2+%3];" : "=r"(v.x), "=r"(v.y) : "r"(a), "n"(OFF));
     return v;
 }
 
-// The four corners of an update from two pair loads.  Pair = (left, right).
+// The interpolated projection value fx of one update from its staged
+// element(s).  e0: the element of row iv (pair column iu + 1); e1: the
+// element of row iv + 1 (pair images only).  fu, fv: the fractions.
 template <int KIND>
-struct Pairs;
+struct Interp;
 
 template <>
-struct Pairs<kPairF32> {
-    using T = float2;
-    static constexpr bool kDiff = true;   // (left, right - left)
-    __device__ static float2 unpack(float2 p) { return p; }
-    template <int OFF>
-    __device__ static float2 load(uint32_t a) { return lds_f2<OFF>(a); }
+struct Interp<kPairF32> {
+    static constexpr bool kQuad = false;
+    __device__ static float fx(uint2 e0, uint2 e1, float fu, float fv)
+    {
+        const float t = fmaf(fu, __uint_as_float(e0.y), __uint_as_float(e0.x));
+        const float bt = fmaf(fu, __uint_as_float(e1.y), __uint_as_float(e1.x));
+        return fmaf(fv, bt - t, t);
+    }
 };
 
-// 16-bit pairs unpack to (left, right - left) as well: the left pixel
-// widened to float32, and the difference by one mixed-precision subtraction
-// (the 16-bit right pixel widened exactly, minus the float32 left, rounded
-// once: the float32 subtraction the texture kernel performs on the same two
-// widened values).
+// (t, b) = (tl, bl) + fu (dt, db) as one two-lane FMA in the storage type,
+// then fx = t + fv (b - t) with b - t by one mixed-precision subtraction
+// (the 16-bit b widened exactly, minus the float32 t, rounded once).
 template <>
-struct Pairs<kPairF16> {
-    using T = unsigned int;
-    static constexpr bool kDiff = true;
-    __device__ static float2 unpack(unsigned int p)
+struct Interp<kQuadF16> {
+    static constexpr bool kQuad = true;
+    __device__ static float fx(uint2 e0, uint2, float fu, float fv)
     {
-        float l, d;
+        unsigned f2, tb;
+        float t, d;
+        asm("cvt.rn.f16x2.f32 %0, %1, %1;" : "=r"(f2) : "f"(fu));
+        asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(tb) : "r"(f2), "r"(e0.y), "r"(e0.x));
         asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.f16 %0, lo;\n\t"
             "sub.rn.f32.f16 %1, hi, %0;\n\t}"
-            : "=f"(l), "=f"(d) : "r"(p));
-        return make_float2(l, d);
+            : "=f"(t), "=f"(d) : "r"(tb));
+        return fmaf(fv, d, t);
     }
-    template <int OFF>
-    __device__ static float2 load(uint32_t a) { return unpack(lds_u32<OFF>(a)); }
 };
 
 template <>
-struct Pairs<kPairBF16> {
-    using T = unsigned int;
-    static constexpr bool kDiff = true;
-    __device__ static float2 unpack(unsigned int p)
+struct Interp<kQuadBF16> {
+    static constexpr bool kQuad = true;
+    __device__ static float fx(uint2 e0, uint2, float fu, float fv)
     {
-        float l, d;
+        unsigned f2, tb;
+        float t, d;
+        asm("cvt.rn.bf16x2.f32 %0, %1, %1;" : "=r"(f2) : "f"(fu));
+        asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(tb) : "r"(f2), "r"(e0.y), "r"(e0.x));
         asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.bf16 %0, lo;\n\t"
             "sub.rn.f32.bf16 %1, hi, %0;\n\t}"
-            : "=f"(l), "=f"(d) : "r"(p));
-        return make_float2(l, d);
+            : "=f"(t), "=f"(d) : "r"(tb));
+        return fmaf(fv, d, t);
     }
-    template <int OFF>
-    __device__ static float2 load(uint32_t a) { return unpack(lds_u32<OFF>(a)); }
 };
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // Shared-memory stride of a ring stage: the box rounded up to a multiple of
 // 128 bytes, the alignment a tensor copy's shared-memory destination needs.
-template <int KIND>
+template <int KIND, int ZPL>
 struct TmaStage {
-    static constexpr int kBytes = (int)sizeof(typename Pairs<KIND>::T) * TmaBox<KIND>::BU * TmaBox<KIND>::BV;
-    static constexpr int kElems = ((kBytes + 127) / 128 * 128) / (int)sizeof(typename Pairs<KIND>::T);
-    static_assert(kElems * (int)sizeof(typename Pairs<KIND>::T) % 128 == 0, "stage stride must be 128-byte aligned");
+    static constexpr int BU = kTmaBU;
+    static constexpr int BV = tma_rows(ZPL, Interp<KIND>::kQuad);
+    static constexpr int kBytes = 8 * BU * BV;
+    static constexpr int kElems = (kBytes + 127) / 128 * 128 / 8;
+    static_assert(kElems * 8 % 128 == 0, "stage stride must be 128-byte aligned");
+    // the brick's sums staged for the float4 epilogue: rows of 32 voxels at a
+    // pitch of 40 floats (the 4 y-rows of a warp land 8 banks apart)
+    static constexpr int kSumPitch = 40;
+    static_assert(kTmaStages * kElems * 8 >= kSumPitch * kBrickY * 2 * ZPL * 4, "sums must fit the ring");
 };
 
-// The 16 updates of one consumer lane for projection i (matrix rows ru, rv,
-// rw), reading the corner pairs from the staged tile (SMEM) or from the
-// global pair image; the two forms are separate loop bodies so neither
-// carries the other's work.  Lane voxels: X[kx] (kx = 0..3, 8 apart), one
-// Y, Z[kz] (kz = 0..3, adjacent); absolute, or offsets from the brick
-// centre with per-brick centring.  The row terms nest z outside y (as the
-// texture kernel does), so the y term is formed once per projection.
-template <int KIND, bool IEEE, bool SMEM>
+// The 4 ZPL updates of one consumer lane for projection i (matrix rows ru,
+// rv, rw), reading the staged box (SMEM) or the global image; the two forms
+// are separate loop bodies so neither carries the other's work.  Lane
+// voxels: X[kx] (kx = 0..3, 8 apart), one Y, Z[q] (q < ZPL, adjacent);
+// absolute, or offsets from the brick centre with per-brick centring.  The
+// row terms nest z outside y, so the y term is formed once per projection.
+template <int KIND, int ZPL, bool IEEE, bool SMEM>
 __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const float4 ru, const float4 rv,
-                                            const float4 rw, int4 mt, uint32_t tile, const float (&X)[4],
-                                            const float Y, const float (&Z)[4], float (&acc)[16])
+                                            const float4 rw, int4 mt, uint32_t tile, const float (&X)[4], const float Y, const float (&Z)[ZPL],
+                                            float (&acc)[4 * ZPL])
 {
-    using P = Pairs<KIND>;
-    using T = typename P::T;
-    constexpr int BU = TmaBox<KIND>::BU;
+    using I = Interp<KIND>;
+    constexpr int BU = kTmaBU;
     // mt is the box decision (1, off, cx0, ry0) or (2, cu, cv, 0).  SMEM:
     // off holds the bits of (row offset) * BU + (column offset) + 1.5 * 2^23,
-    // so fv0 * BU + fu0 + off is the element index of the top pair in the
-    // staged box, plus the magic, exactly (all integers far below 2^22); its
-    // bits times the pair size, plus (tile - magic bits * pair size) modulo
-    // 2^32, are the shared address.  Global: pair column floor(u') + cu, top
-    // row floor(v') + cv.
+    // so fv0 * BU + fu0 + off is the element index in the staged box, plus
+    // the magic, exactly (all integers far below 2^22); its bits times 8,
+    // plus (tile - magic bits * 8) modulo 2^32, are the shared address.
+    // Global: element column floor(u') + cu, stored row floor(v') + cv.
     const float off = __int_as_float(mt.y);
-    const uint32_t base = tile - kIntMagicBits * (uint32_t)sizeof(T);
+    const uint32_t base = tile - kIntMagicBits * 8u;
     const float cu = fmaf(ru.y, Y, ru.w), cv = fmaf(rv.y, Y, rv.w), cw = fmaf(rw.y, Y, rw.w);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < ZPL; ++q) {
         const float bu = fmaf(ru.z, Z[q], cu);
         const float bv = fmaf(rv.z, Z[q], cv);
         const float bw = fmaf(rw.z, Z[q], cw);
@@ -228,65 +243,63 @@ __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const floa
             const float r = recip_tma<IEEE>(w);
             const float u = uw * r, v = vw * r;
             const float fu0 = floorf(u), fv0 = floorf(v);
-            float2 top, bot;
+            uint2 e0, e1 = make_uint2(0u, 0u);
             if constexpr (SMEM) {
                 // every lane's coordinates lie in the volume (clamped at
                 // setup) and the box covers the brick's footprint with a pixel
                 // of margin, so the address is inside the staged box
                 const float e = fmaf(fv0, (float)BU, fu0 + off);
-                const uint32_t a = (uint32_t)__float_as_int(e) * (uint32_t)sizeof(T) + base;
-                top = P::template load<0>(a);
-                bot = P::template load<BU * (int)sizeof(T)>(a);
+                const uint32_t a = (uint32_t)__float_as_int(e) * 8u + base;
+                e0 = lds_u2<0>(a);
+                if constexpr (!I::kQuad)
+                    e1 = lds_u2<BU * 8>(a);
             } else {
-                // rows outside the detector are zero
+                // stored rows outside the image are zero (the TMA fill)
                 const int col = int_of_integral(fu0) + mt.y;
                 const int row = int_of_integral(fv0) + mt.z;
-                const T *img = reinterpret_cast<const T *>(b.img[i]);
+                const int rows = tma_image_rows(I::kQuad ? kQuadF16 : kPairF32, b.isy);
+                const uint2 *img = reinterpret_cast<const uint2 *>(b.img[i]);
                 const bool cok = col >= 0 && col <= b.isx;
-                const T *p = img + (long long)row * b.pitch + col;
-                const T zero{};
-                top = P::unpack(cok && row >= 0 && row < b.isy ? p[0] : zero);
-                bot = P::unpack(cok && row + 1 >= 0 && row + 1 < b.isy ? p[b.pitch] : zero);
+                const uint2 *p = img + (long long)row * b.pitch + col;
+                const uint2 zero = make_uint2(0u, 0u);
+                e0 = cok && row >= 0 && row < rows ? p[0] : zero;
+                if constexpr (!I::kQuad)
+                    e1 = cok && row + 1 >= 0 && row + 1 < rows ? p[b.pitch] : zero;
             }
             const float fu = u - fu0, fv = v - fv0;
-            const float dt = P::kDiff ? top.y : top.y - top.x;
-            const float db = P::kDiff ? bot.y : bot.y - bot.x;
-            const float t = fmaf(fu, dt, top.x);
-            const float bt = fmaf(fu, db, bot.x);
-            const float fx = fmaf(fv, bt - t, t);
+            const float fx = I::fx(e0, e1, fu, fv);
             acc[q * 4 + kx] = fmaf(fx, r * r, acc[q * 4 + kx]);
         }
     }
 }
 
-// Warp-specialised pipeline: warps 0..7 compute (256 consumer threads, 16
-// voxels each), warp 8 is the producer.  Stage s of the S-deep ring
-// has a "full" barrier (the producer's arrival, plus the TMA bytes when a
-// tile is loaded) and an "empty" barrier (one arrival per consumer warp when
-// it is done with the stage).  No block-wide barrier inside the loop.
+// Warp-specialised pipeline: warps 0..7 compute (256 consumer threads,
+// 4 ZPL voxels each), warp 8 is the producer.  Stage s of the ring has a
+// "full" barrier (the producer's arrival, plus the TMA bytes when a tile is
+// loaded) and an "empty" barrier (one arrival per consumer warp when it is
+// done with the stage).  No block-wide barrier inside the loop.
 // BLK: per-brick centring; the block stages the brick's centring records
 // (u row, v row, (w_c, ku_b, kv_b)) of every projection in shared memory at
 // the start, and consumers work with offsets from the brick centre, as the
 // texture kernel does per block.
-template <int KIND, bool IEEE, bool BLK>
-__global__ void __launch_bounds__(kThreads + 32, 3)
+template <int KIND, bool IEEE, bool BLK, int ZPL>
+__global__ void __launch_bounds__(kThreads + 32, ZPL == 4 ? 3 : 2)
 bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const VolGeom g, int accumulate,
               int *__restrict__ err, unsigned long long *__restrict__ work)
 {
-    using P = Pairs<KIND>;
-    using T = typename P::T;
-    constexpr int BU = TmaBox<KIND>::BU, BV = TmaBox<KIND>::BV;
-    constexpr int kBufElems = BU * BV;                  // pairs one box copy writes
-    constexpr int kStageElems = TmaStage<KIND>::kElems;   // stage stride: 128-byte multiple
-    constexpr int S = TmaBox<KIND>::S;
+    using St = TmaStage<KIND, ZPL>;
+    constexpr int kBufElems = St::BU * St::BV;       // elements one box copy writes
+    constexpr int kStageElems = St::kElems;         // stage stride: 128-byte multiple
+    constexpr int S = kTmaStages;
+    constexpr int BZ = 2 * ZPL;
     constexpr int kConsumerWarps = kThreads / 32;
     // consumer layout: 8 x-lanes by 4 y-lanes per warp, warps 0-3 and 4-7
-    // on the two 4-deep z halves; each lane 4 voxels along x (8 apart) and
-    // 4 along z, covering the brick once
-    static_assert(kBrickX == 8 * 4 && kBrickY == 4 * 4 && kBrickZ == 2 * 4 && kConsumerWarps == 8,
-                  "the consumer layout tiles a 32 x 16 x 8 brick with 8 warps");
-    extern __shared__ __align__(128) unsigned char dyn_smem[];   // the ring: S stages of kStageElems pairs
-    T (*buf)[kStageElems] = reinterpret_cast<T (*)[kStageElems]>(dyn_smem);
+    // on the two ZPL-deep z halves; each lane 4 voxels along x (8 apart) and
+    // ZPL along z, covering the brick once
+    static_assert(kBrickX == 8 * 4 && kBrickY == 4 * 4 && kConsumerWarps == 8,
+                  "the consumer layout tiles a 32 x 16 x 2 ZPL brick with 8 warps");
+    extern __shared__ __align__(128) unsigned char dyn_smem[];   // the ring: S stages of kStageElems
+    uint2(*buf)[kStageElems] = reinterpret_cast<uint2(*)[kStageElems]>(dyn_smem);
     __shared__ __align__(8) uint64_t full[S], empty[S];
     // the brick's box decision for every projection of the batch (made by
     // the pre-pass: culled / staged box / global path, with its offsets),
@@ -298,7 +311,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = g.L;
-    const int bx0 = blockIdx.x * kBrickX, by0 = blockIdx.y * kBrickY, bz0 = blockIdx.z * kBrickZ;
+    const int bx0 = blockIdx.x * kBrickX, by0 = blockIdx.y * kBrickY, bz0 = blockIdx.z * BZ;
     const size_t brick = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 
     if (threadIdx.x == 0) {
@@ -344,8 +357,8 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                 break;
             ++computed;
             if (bi.x == 1) {
-                mbar_expect_tx(&full[st], (uint32_t)(kBufElems * sizeof(T)));
-                tma_load_2d(buf[st], &b.map[i], bi.z * kPairWords<KIND>, bi.w, &full[st]);
+                mbar_expect_tx(&full[st], (uint32_t)(kBufElems * 8));
+                tma_load_2d(buf[st], &b.map[i], bi.z * 2, bi.w, &full[st]);
                 issued |= 1 << st;
                 last_par = (last_par & ~(1u << st)) | ((unsigned)(use & 1) << st);
             } else {
@@ -355,7 +368,7 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
         }
         if (computed) {
             const int xe = min(bx0 + kBrickX, L) - 1, ye = min(by0 + kBrickY, L) - 1;
-            const int ze = min(bz0 + kBrickZ, g.Lz) - 1;
+            const int ze = min(bz0 + BZ, g.Lz) - 1;
             atomicAdd(work, computed * (unsigned long long)((xe - bx0 + 1) * (ye - by0 + 1) * (ze - bz0 + 1)));
         }
         if (*(volatile int *)&abort_flag) {
@@ -373,31 +386,35 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     // them, which keeps the shared-memory bank conflicts of the corner loads
     // low (a z-spread warp spans rows whose pitch aliases the banks).
     const int tx = lane & 7, ty = lane >> 3;
-    // this lane's voxels: x0 + {0, 8, 16, 24}, y0, z0 + {0, 1, 2, 3};
+    const int yl = 4 * (warp & 3) + ty, zl0 = ZPL * (warp >> 2);
+    // this lane's voxels: x0 + {0, 8, 16, 24}, y0, z0 + {0 .. ZPL-1};
     // lanes beyond a ragged edge compute with the last voxel's coordinates
     // (inside the brick box, so their loads stay in the staged tile) and
     // store nothing
     // (BLK: offsets from the centre of the brick's voxel box clipped to the
     // volume, (x0 + x1) / 2 etc., a multiple of 1/2, as in the pre-pass)
-    const int x0 = bx0 + tx, y0 = by0 + 4 * (warp & 3) + ty, z0 = bz0 + 4 * (warp >> 2);
+    const int x0 = bx0 + tx, y0 = by0 + yl, z0 = bz0 + zl0;
     const float hx = 0.5f * (float)(bx0 + min(bx0 + kBrickX, L) - 1);
     const float hy = 0.5f * (float)(by0 + min(by0 + kBrickY, L) - 1);
-    const float hz = 0.5f * (float)(bz0 + min(bz0 + kBrickZ, g.Lz) - 1);
-    float X[4], Z[4];
+    const float hz = 0.5f * (float)(bz0 + min(bz0 + BZ, g.Lz) - 1);
+    float X[4], Z[ZPL];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int x = min(x0 + 8 * k, L - 1), z = min(z0 + k, g.Lz - 1);
+        const int x = min(x0 + 8 * k, L - 1);
         X[k] = BLK ? g.R * ((float)x - hx) : fmaf(g.R, (float)x, g.Ox);
-        Z[k] = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)z, g.Oz);
+    }
+#pragma unroll
+    for (int q = 0; q < ZPL; ++q) {
+        const int z = min(z0 + q, g.Lz - 1);
+        Z[q] = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)z, g.Oz);
     }
     const int yc = min(y0, L - 1);
     const float Y = BLK ? g.R * ((float)yc - hy) : fmaf(g.R, (float)yc, g.Oy);
 
-    float acc[16];
+    float acc[4 * ZPL];
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < 4 * ZPL; ++k)
         acc[k] = 0.f;
-    bool ok = true;
     int s = 0;
     uint32_t phase = 0;
 #pragma unroll 1
@@ -410,7 +427,6 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                 atomicExch(&abort_flag, 1);
                 atomicExch(err, 1);
             }
-            ok = false;
             break;
         }
         {
@@ -424,9 +440,9 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
                 rv = b.m[i][1];
             }
             if (mt.x == 1)   // tile in shared memory (the common case)
-                tma_updates<KIND, IEEE, true>(b, i, ru, rv, rw, mt, smem_u32(buf[s]), X, Y, Z, acc);
+                tma_updates<KIND, ZPL, IEEE, true>(b, i, ru, rv, rw, mt, smem_u32(buf[s]), X, Y, Z, acc);
             else             // footprint larger than the tile
-                tma_updates<KIND, IEEE, false>(b, i, ru, rv, rw, mt, 0u, X, Y, Z, acc);
+                tma_updates<KIND, ZPL, IEEE, false>(b, i, ru, rv, rw, mt, 0u, X, Y, Z, acc);
         }
         __syncwarp();
         if (lane == 0)
@@ -437,47 +453,85 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
         }
     }
 
-    if (!ok)
+    // Every consumer warp is past its last wait, so every copy the producer
+    // issued has landed and the ring is free.
+    consumers_sync();
+    if (*(volatile int *)&abort_flag)
         return;
-    // the volume's read-modify-write; with final_out the same values also go
-    // to the caller's destination (mapped host memory: the read-back of the
-    // finished volume then overlaps this launch instead of following it)
+    // The brick's sums, staged as rows of 32 voxels (x fastest), then the
+    // volume's read-modify-write with float4 accesses: 8 threads per row of
+    // 32 voxels.  With final_out the same values also go to the caller's
+    // destination (mapped host memory: the read-back of the finished volume
+    // then overlaps this launch instead of following it).
+    float *sums = reinterpret_cast<float *>(dyn_smem);
+    constexpr int P = St::kSumPitch;
+#pragma unroll
+    for (int q = 0; q < ZPL; ++q)
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx)
+            sums[((zl0 + q) * kBrickY + yl) * P + tx + 8 * kx] = acc[q * 4 + kx];
+    consumers_sync();
     float *const fin = b.final_out;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int y = y0, z = z0 + q;
-        if (y >= L || z >= g.Lz)
+    for (int f = threadIdx.x; f < kBrickX / 4 * kBrickY * BZ; f += kThreads) {
+        const int xq = f & 7, ys = (f >> 3) % kBrickY, zs = (f >> 3) / kBrickY;
+        const int x = bx0 + 4 * xq, y = by0 + ys, z = bz0 + zs;
+        if (y >= L || z >= g.Lz || x >= L)
             continue;
-        const size_t r0 = ((size_t)z * L + y) * L;
-        float *row = vol + r0;
+        const float4 a = *reinterpret_cast<const float4 *>(&sums[(zs * kBrickY + ys) * P + 4 * xq]);
+        const size_t o = ((size_t)z * L + y) * L + x;
+        if (b.vec4 && x + 3 < L) {
+            float4 v = a;
+            if (accumulate) {
+                const float4 old = *reinterpret_cast<const float4 *>(vol + o);
+                v = make_float4(old.x + a.x, old.y + a.y, old.z + a.z, old.w + a.w);
+            }
+            *reinterpret_cast<float4 *>(vol + o) = v;
+            if (fin)
+                *reinterpret_cast<float4 *>(fin + o) = v;
+        } else {
+            const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-        for (int kx = 0; kx < 4; ++kx) {
-            const int x = x0 + 8 * kx;
-            if (x < L) {
-                const float v = (accumulate ? row[x] : 0.f) + acc[q * 4 + kx];
-                row[x] = v;
-                if (fin)
-                    fin[r0 + x] = v;
+            for (int j = 0; j < 4; ++j) {
+                if (x + j < L) {
+                    const float v = (accumulate ? vol[o + j] : 0.f) + av[j];
+                    vol[o + j] = v;
+                    if (fin)
+                        fin[o + j] = v;
+                }
             }
         }
     }
+}
+
+template <int KIND, bool IEEE, bool BLK, int ZPL>
+static cudaError_t launch_tma_zpl(const TmaBatch &b, float *vol, const VolGeom &g, bool acc, int *err,
+                                  unsigned long long *work, cudaStream_t s)
+{
+    dim3 grid((g.L + kBrickX - 1) / kBrickX, (g.L + kBrickY - 1) / kBrickY, (g.Lz + 2 * ZPL - 1) / (2 * ZPL));
+    const size_t smem = 8 * (size_t)TmaStage<KIND, ZPL>::kElems * kTmaStages;
+    // the ring exceeds the 48 KB default (set per call: cheap, and correct
+    // on whichever device is current)
+    cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<KIND, IEEE, BLK, ZPL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    bp_tma_kernel<KIND, IEEE, BLK, ZPL><<<grid, kThreads + 32, smem, s>>>(b, vol, g, acc ? 1 : 0, err, work);
+    return cudaGetLastError();
 }
 
 template <int KIND, bool IEEE, bool BLK>
 static cudaError_t launch_tma_blk(const TmaBatch &b, float *vol, const VolGeom &g, bool acc, int *err,
                                   unsigned long long *work, cudaStream_t s)
 {
-    dim3 grid((g.L + kBrickX - 1) / kBrickX, (g.L + kBrickY - 1) / kBrickY, (g.Lz + kBrickZ - 1) / kBrickZ);
-    using T = typename Pairs<KIND>::T;
-    const size_t smem = sizeof(T) * TmaStage<KIND>::kElems * TmaBox<KIND>::S;
-    // the ring exceeds the 48 KB default for float32 pairs (set per call:
-    // cheap, and correct on whichever device is current)
-    cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<KIND, IEEE, BLK>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    bp_tma_kernel<KIND, IEEE, BLK><<<grid, kThreads + 32, smem, s>>>(b, vol, g, acc ? 1 : 0, err, work);
-    return cudaGetLastError();
+    switch (b.zpl) {
+    case 8:
+        return launch_tma_zpl<KIND, IEEE, BLK, 8>(b, vol, g, acc, err, work, s);
+    case 6:
+        return launch_tma_zpl<KIND, IEEE, BLK, 6>(b, vol, g, acc, err, work, s);
+    default:
+        return launch_tma_zpl<KIND, IEEE, BLK, 4>(b, vol, g, acc, err, work, s);
+    }
 }
 
 // Per-brick centring exists for the float32 pairs only (16-bit storage
@@ -498,46 +552,68 @@ cudaError_t launch_bp_tma(const TmaBatch &b, float *vol, const VolGeom &g, int p
 {
     if (b.n <= 0)
         return cudaSuccess;
+    if (b.zpl != 4 && b.zpl != 6 && b.zpl != 8)
+        return cudaErrorInvalidValue;
     switch (pair_kind) {
     case kPairF32:
         return ieee_rcp ? launch_tma_kind<kPairF32, true>(b, vol, g, accumulate, err, work, s)
                         : launch_tma_kind<kPairF32, false>(b, vol, g, accumulate, err, work, s);
-    case kPairF16:
-        return ieee_rcp ? launch_tma_kind<kPairF16, true>(b, vol, g, accumulate, err, work, s)
-                        : launch_tma_kind<kPairF16, false>(b, vol, g, accumulate, err, work, s);
+    case kQuadF16:
+        return ieee_rcp ? launch_tma_kind<kQuadF16, true>(b, vol, g, accumulate, err, work, s)
+                        : launch_tma_kind<kQuadF16, false>(b, vol, g, accumulate, err, work, s);
     default:
-        return ieee_rcp ? launch_tma_kind<kPairBF16, true>(b, vol, g, accumulate, err, work, s)
-                        : launch_tma_kind<kPairBF16, false>(b, vol, g, accumulate, err, work, s);
+        return ieee_rcp ? launch_tma_kind<kQuadBF16, true>(b, vol, g, accumulate, err, work, s)
+                        : launch_tma_kind<kQuadBF16, false>(b, vol, g, accumulate, err, work, s);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Pair images: element c of row k holds (p[k][c-1], p[k][c]) for
-// c = 0 .. isx (zero outside the detector), in the storage type, or for
-// float32 (p[k][c-1], p[k][c] - p[k][c-1]); elements c > isx of the padded
-// row are zero.  One thread per element.
+// Staged images, one thread per element (zero outside the detector):
+//   float32 pairs: element c of row k = (p[k][c-1], p[k][c] - p[k][c-1]),
+//     rows k = 0 .. isy - 1;
+//   16-bit column quads: element c of stored row j (image row k = j - 1,
+//     j = 0 .. isy) = ((p[k][c-1], p[k+1][c-1]), (p[k][c] - p[k][c-1],
+//     p[k+1][c] - p[k+1][c-1])), each value rounded once to the storage
+//     type (the differences taken in float32 first);
+// for c = 0 .. isx; elements c > isx of the padded row are zero.
+__device__ __forceinline__ float pix(const float *src, int isx, int isy, int k, int c)
+{
+    return (k >= 0 && k < isy && c >= 0 && c < isx) ? src[(size_t)k * isx + c] : 0.f;
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256)
 pair_image_kernel(const __grid_constant__ PairBatch b, int isx, int isy, int pitch)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.y;
+    const int j = blockIdx.y;
     const int i = blockIdx.z;
     if (c >= pitch || i >= b.n)
         return;
-    const float *src = b.src[i] + (size_t)k * isx;
-    const float l = (c >= 1 && c <= isx) ? src[c - 1] : 0.f;
-    const float r = (c < isx) ? src[c] : 0.f;
-    const size_t o = (size_t)k * pitch + c;
+    const float *src = b.src[i];
+    const size_t o = (size_t)j * pitch + c;
+    uint2 *dst = reinterpret_cast<uint2 *>(b.dst[i]);
+    const bool in = c <= isx;
     if constexpr (KIND == kPairF32) {
-        reinterpret_cast<float2 *>(b.dst[i])[o] = make_float2(l, __fsub_rn(r, l));
-    } else if constexpr (KIND == kPairF16) {
-        const __half2 h = __floats2half2_rn(l, r);
-        reinterpret_cast<__half2 *>(b.dst[i])[o] = h;
+        const float l = in ? pix(src, isx, isy, j, c - 1) : 0.f;
+        const float r = in ? pix(src, isx, isy, j, c) : 0.f;
+        dst[o] = make_uint2(__float_as_uint(l), __float_as_uint(__fsub_rn(r, l)));
     } else {
-        const unsigned int lo = __bfloat16_as_ushort(__float2bfloat16_rn(l));
-        const unsigned int hi = __bfloat16_as_ushort(__float2bfloat16_rn(r));
-        reinterpret_cast<unsigned int *>(b.dst[i])[o] = lo | (hi << 16);
+        const int k = j - 1;
+        const float tl = in ? pix(src, isx, isy, k, c - 1) : 0.f, tr = in ? pix(src, isx, isy, k, c) : 0.f;
+        const float bl = in ? pix(src, isx, isy, k + 1, c - 1) : 0.f, br = in ? pix(src, isx, isy, k + 1, c) : 0.f;
+        const float dt = __fsub_rn(tr, tl), db = __fsub_rn(br, bl);
+        unsigned lo, hi;
+        if constexpr (KIND == kQuadF16) {
+            lo = (unsigned)__half_as_ushort(__float2half_rn(tl)) | ((unsigned)__half_as_ushort(__float2half_rn(bl)) << 16);
+            hi = (unsigned)__half_as_ushort(__float2half_rn(dt)) | ((unsigned)__half_as_ushort(__float2half_rn(db)) << 16);
+        } else {
+            lo = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(tl)) |
+                 ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(bl)) << 16);
+            hi = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(dt)) |
+                 ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(db)) << 16);
+        }
+        dst[o] = make_uint2(lo, hi);
     }
 }
 
@@ -545,13 +621,13 @@ cudaError_t launch_pair_images(const PairBatch &b, int isx, int isy, int pitch, 
 {
     if (b.n <= 0)
         return cudaSuccess;
-    dim3 grid((pitch + 255) / 256, isy, b.n);
+    dim3 grid((pitch + 255) / 256, tma_image_rows(pair_kind, isy), b.n);
     if (pair_kind == kPairF32)
         pair_image_kernel<kPairF32><<<grid, 256, 0, s>>>(b, isx, isy, pitch);
-    else if (pair_kind == kPairF16)
-        pair_image_kernel<kPairF16><<<grid, 256, 0, s>>>(b, isx, isy, pitch);
+    else if (pair_kind == kQuadF16)
+        pair_image_kernel<kQuadF16><<<grid, 256, 0, s>>>(b, isx, isy, pitch);
     else
-        pair_image_kernel<kPairBF16><<<grid, 256, 0, s>>>(b, isx, isy, pitch);
+        pair_image_kernel<kQuadBF16><<<grid, 256, 0, s>>>(b, isx, isy, pitch);
     return cudaGetLastError();
 }
 

@@ -10,11 +10,13 @@ import pytest
 from paper_1104_5243_gb300 import _native as N
 from paper_1104_5243_gb300 import build as B
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bp1104.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+HEADER = os.path.join(INCLUDE, "bp1104.h")
+HEADER_F64 = os.path.join(INCLUDE, "bp1104_f64.h")
 
 
-def declared_symbols():
-    text = open(HEADER).read()
+def declared_symbols(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(bp_[a-z0-9_]+)\s*\(", text)))
 
@@ -41,10 +43,38 @@ def test_binding_covers_exactly_the_header():
     assert sorted(N.SIGNATURES) == declared_symbols()
 
 
+def needed_libraries(path):
+    """DT_NEEDED entries of a shared object's dynamic section (readelf -d)."""
+    import subprocess
+    out = subprocess.run(["readelf", "-d", path], capture_output=True, text=True, check=True).stdout
+    return re.findall(r"\(NEEDED\)\s+Shared library: \[([^\]]+)\]", out)
+
+
 def test_library_links_no_torch(lib):
-    # the ABI is plain C: the shared object must not depend on libtorch/c10
-    data = open(N.library_path(), "rb").read()
-    assert b"libtorch" not in data and b"libc10" not in data
+    # the ABI is plain C: neither shared object may depend on libtorch/c10
+    for path in (N.library_path(), B.build_f64()):
+        needed = needed_libraries(path)
+        assert needed, path
+        assert not any("torch" in n or "c10" in n for n in needed), needed
+
+
+def test_f64_check_library_exports_its_header():
+    """The float64 gradient-check library (test support) exports exactly what
+    include/bp1104_f64.h declares, and its binding covers it."""
+    from paper_1104_5243_gb300 import _f64
+    B.build_f64()
+    f64 = _f64.lib()
+    syms = declared_symbols(HEADER_F64)
+    assert syms == sorted(_f64.SIGNATURES)
+    for name in syms:
+        assert hasattr(f64, name), name
+    # host-side validation, before any CUDA call
+    O = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    assert f64.bp_f64_backproject(0, 1.0, O, 8, 8, None, None, 1, None, None) == N.BP_EINVAL
+    assert f64.bp_f64_adjoint(8, 1.0, O, 8, 8, None, None, 1, None, None) == N.BP_EINVAL
+    assert b"bp_f64_adjoint" in f64.bp_f64_last_error()
+    # the product library holds no float64 kernel entry point
+    assert not any(name.startswith("bp_f64") for name in declared_symbols())
 
 
 def test_create_rejects_bad_sizes_without_touching_the_gpu(lib):

@@ -125,15 +125,42 @@ def test_two_gloo_ranks_share_one_volume_by_z_slabs():
 
 
 def test_adjoint_roofline_bounds():
-    """The adjoint's bounds: issue at the measured instructions per update,
-    shared-memory atomics at four per update with the measured wavefronts per
-    atomic instruction, one wavefront per SM per clock."""
+    """The adjoint's roofline comes from the method's work alone: FP32 pipe
+    at 20.5 operations per update, four conflict-free shared-memory atomics
+    per update (one wavefront per SM per clock), one reciprocal per update.
+    The measured instruction and wavefront counts stay diagnostics."""
     sys.path.insert(0, ROOT)
     import bench
     b = bench.adjoint_roofline_gups(2000.0, 100)
-    assert b["issue"] == pytest.approx(100 * 128 / bench.ADJ_INSTR_PER_UPDATE * 2.0)
-    assert b["smem_atomics"] == pytest.approx(100 * 2.0 * 32 / (4 * bench.ADJ_ATOMIC_WAVEFRONTS))
-    assert b["min"] == min(b["issue"], b["smem_atomics"])
+    assert b["fp32_pipe"] == pytest.approx(100 * 128 / 20.5 * 2.0)
+    assert b["smem_atomics"] == pytest.approx(100 * 2.0 * 32 / 4)
+    assert b["mufu"] == pytest.approx(100 * 16 * 2.0)
+    assert b["min"] == min(b["fp32_pipe"], b["smem_atomics"], b["mufu"])
+    d = bench.adjoint_diagnostics_gups(2000.0, 100)
+    assert d["issue_at_measured_instr"] == pytest.approx(100 * 128 / bench.ADJ_INSTR_PER_UPDATE * 2.0)
+    assert d["smem_atomics_at_measured_wavefronts"] == pytest.approx(
+        100 * 2.0 * 32 / (4 * bench.ADJ_ATOMIC_WAVEFRONTS))
+
+
+def test_forward_roofline_is_the_methods_work():
+    """The backprojection's peak at 152 SMs and 2070 MHz: FP32 pipe at 20.5
+    operations per update (1965 GUP/s) binds both storage forms on the TMA
+    path; shared memory at 16 B (f32) or 8 B (16-bit) per update and MUFU are
+    looser.  No kernel-measured count enters the peak, so instructions the
+    kernel adds cannot raise it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for form, smem in (("f32", 16), ("f16", 8), ("bf16", 8)):
+        b = bench.roofline_peak_gups("tma", form, 2070.0, 152, 0.0)
+        assert b["fp32_pipe"] == pytest.approx(152 * 128 / 20.5 * 2.07)
+        assert b["smem"] == pytest.approx(152 * 128 / smem * 2.07)
+        assert b["mufu"] == pytest.approx(152 * 16 * 2.07)
+        assert b["min"] == pytest.approx(1965.0, rel=1e-3)
+        assert "issue" not in b
+    t = bench.roofline_peak_gups("texture", "f32", 2070.0, 152, 2.54)
+    assert t["min"] == pytest.approx(t["gather"]) and t["gather"] == pytest.approx(152 * 2.54 * 2.07)
+    d = bench.roofline_diagnostics_gups("tma", "f32", 2070.0, 152)
+    assert d["issue_at_measured_instr"] == pytest.approx(152 * 128 / bench.INSTR_PER_UPDATE[("tma", "f32")] * 2.07)
 
 
 def test_ncu_fields_need_every_name_and_the_current_source(tmp_path, monkeypatch):

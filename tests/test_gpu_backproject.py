@@ -258,20 +258,25 @@ def test_full_detector_ramp_filtered_phantom(dtype, tol, path):
 
 
 # ---------------------------------------------------------------------------
-# TMA / shared-memory data path: same arithmetic as the texture path with
-# per-projection centring, so the volumes agree bit for bit (culled bricks
-# only skip exact zeros).
-def run_path(vol, scan, A, q, path, dtype="f32", block_centre=None):
+# TMA / shared-memory data path: for float32 projections the same arithmetic
+# as the texture path with per-projection centring, so the volumes agree bit
+# for bit (culled bricks only skip exact zeros); 16-bit storage rounds each
+# staged pixel difference once on the TMA path (the texture path differences
+# the rounded pixels), so there the two paths agree to the storage rounding.
+def run_path(vol, scan, A, q, path, dtype="f32", block_centre=None, depth=None):
     """block_centre=None keeps the default (per-block centring for float32
     projections, with the texture kernel's blocks or the TMA path's bricks as
     the blocks); bit-identity between the paths needs block_centre=0 on both
-    for float32 projections."""
+    for float32 projections.  depth: the TMA path's brick depth (None:
+    automatic)."""
     api = native()
     from paper_1104_5243_gb300 import _native as N
     bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype)
     bp.set_option(N.BP_OPT_PATH, path)
     if block_centre is not None:
         bp.set_option(N.BP_OPT_BLOCK_CENTRE, block_centre)
+    if depth is not None:
+        bp.set_option(N.BP_OPT_BRICK_DEPTH, depth)
     bp.add_projections(torch.from_numpy(np.ascontiguousarray(q)).cuda(), A)
     out = bp.finalize().cpu()
     taken = bp.last_path
@@ -280,20 +285,46 @@ def run_path(vol, scan, A, q, path, dtype="f32", block_centre=None):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-def test_tma_path_is_bit_identical_to_texture_path(dtype):
+def test_tma_path_against_texture_path(dtype):
     scan, vol, A, ell, q, ref = tiny_phantom_case()
     tex, p1 = run_path(vol, scan, A, q, 1, dtype, block_centre=0)
     tma, p2 = run_path(vol, scan, A, q, 2, dtype, block_centre=0)
     assert (p1, p2) == ("texture", "tma")
-    assert torch.equal(tex, tma)
     tol = {"f32": FP32_TOL, "f16": FP16_TOL, "bf16": BF16_TOL}[dtype]
-    assert rel_l2(tma.numpy(), ref) <= tol
+    e_tex, e_tma = rel_l2(tex.numpy(), ref), rel_l2(tma.numpy(), ref)
+    print(f"{dtype}: rel-L2 texture {e_tex:.3e}, TMA {e_tma:.3e}, max-abs TMA "
+          f"{np.abs(tma.numpy() - ref).max():.3e}")
+    if dtype == "f32":
+        assert torch.equal(tex, tma)
+    else:
+        # both within the storage bar; the TMA path's two-lane FMA rounds
+        # the row values once more to the storage type, which about doubles
+        # the storage error on this ramp-filtered phantom (measured 1.6e-4
+        # against 8.3e-5 for f16, 1.2e-3 against 6.4e-4 for bf16)
+        assert e_tma <= tol and e_tex <= tol
+        assert e_tma <= 2.5 * e_tex
     # the defaults (per-block centring for float32) match the oracle too
-    for path in (1, 2):
+    for path, fixed in ((1, tex), (2, tma)):
         blk, _ = run_path(vol, scan, A, q, path, dtype)
         assert rel_l2(blk.numpy(), ref) <= tol
         if dtype != "f32":
-            assert torch.equal(blk, tex)
+            assert torch.equal(blk, fixed)   # 16-bit storage always centres per projection
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_brick_depths_agree(dtype):
+    """The TMA path's bricks of 32 x 16 x 8, 12 and 16 voxels: with
+    per-projection centring every voxel sums the same float32 terms in the
+    same order, so the volumes agree bit for bit (the depths differ in which
+    bricks are culled and which take the global branch, both exact); with
+    per-brick centring (the float32 default) each matches the oracle."""
+    scan, vol, A, ell, q, ref = tiny_phantom_case()
+    tol = {"f32": FP32_TOL, "f16": FP16_TOL, "bf16": BF16_TOL}[dtype]
+    outs = [run_path(vol, scan, A, q, 2, dtype, block_centre=0, depth=d)[0] for d in (8, 12, 16)]
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    for d in (8, 12, 16):
+        blk, _ = run_path(vol, scan, A, q, 2, dtype, depth=d)
+        assert rel_l2(blk.numpy(), ref) <= tol
 
 
 @pytest.mark.parametrize("L,isx,isy,n", [(37, 53, 41, 70), (1, 7, 5, 3), (40, 24, 10, 20)])
@@ -312,34 +343,52 @@ def test_tma_path_ragged_and_partial_detector(L, isx, isy, n):
         assert rel_l2(blk.numpy(), ref) <= FP32_TOL
 
 
-def test_tma_global_fallback_when_footprints_exceed_the_tile():
+@pytest.mark.parametrize("depth", [8, 16])
+def test_tma_global_fallback_when_footprints_exceed_the_tile(depth):
     """256^3 with the full detector: most brick footprints are larger than the
-    shared-memory tile, so the forced TMA path reads the pair images from
+    shared-memory tile, so the forced TMA path reads the staged images from
     global memory; still bit-identical to the texture path."""
     scan = synth.Scan(n=40, isx=1248, isy=960, pitch=0.308)
     vol = synth.Volume(256)
     A = oracle.carm_matrices(scan)
     q = synth.uniform_stack(scan.n, scan.isy, scan.isx, seed=11)
     tex, _ = run_path(vol, scan, A, q, 1, block_centre=0)
-    tma, _ = run_path(vol, scan, A, q, 2, block_centre=0)
+    tma, _ = run_path(vol, scan, A, q, 2, block_centre=0, depth=depth)
     assert torch.equal(tex, tma)
     idx = np.random.default_rng(1).integers(0, 256 ** 3, size=512)
     ref = oracle.backproject_voxels(vol.L, vol.R, vol.O, q, A, idx)
     assert rel_l2(tma.view(-1).numpy()[idx], ref) <= FP32_TOL
-    blk, _ = run_path(vol, scan, A, q, 2)
+    blk, _ = run_path(vol, scan, A, q, 2, depth=depth)
     assert rel_l2(blk.view(-1).numpy()[idx], ref) <= FP32_TOL
 
 
-@pytest.mark.parametrize("dtype,expect", [("f32", "tma"), ("f16", "tma"), ("bf16", "tma")])
-def test_automatic_path_choice(dtype, expect):
-    """Automatic: the TMA path, the faster on GB300 for every storage type."""
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("L,expect,depth", [(512, "tma", 16), (1024, "tma", 16), (256, "texture", None),
+                                            (128, "texture", None)])
+def test_automatic_path_choice(dtype, L, expect, depth):
+    """Automatic: the TMA path with the deepest brick whose box holds the
+    footprints where voxels are fine (0.5 mm and 0.25 mm on the 1248x960
+    detector: 16-deep bricks), the texture path where they are coarse
+    (1 mm, 2 mm: a brick's footprint is wider than any staged box).  Eight
+    projections of the full scan; the result equals the forced choice."""
+    api = native()
+    from paper_1104_5243_gb300 import _native as N
     scan = synth.SCANS["full"]
     A = oracle.carm_matrices(scan)[:8]
-    q = synth.uniform_stack(8, scan.isy, scan.isx, seed=3)
-    auto, p_auto = run_path(synth.Volume(128), scan, A, q, 0, dtype)
-    forced, p_forced = run_path(synth.Volume(128), scan, A, q, 2 if expect == "tma" else 1, dtype)
-    assert (p_auto, p_forced) == (expect, expect)
-    assert torch.equal(auto, forced)
+    q = torch.from_numpy(synth.uniform_stack(8, scan.isy, scan.isx, seed=3)).cuda()
+    vol = synth.Volume(L)
+    outs = []
+    for path in (0, 2 if expect == "tma" else 1):
+        with api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype) as bp:
+            bp.set_option(N.BP_OPT_PATH, path)
+            if path == 2:
+                bp.set_option(N.BP_OPT_BRICK_DEPTH, depth)
+            bp.add_projections(q, A)
+            assert bp.last_path == expect
+            if expect == "tma":
+                assert bp.query(N.BP_QUERY_LAST_BRICK_DEPTH) == depth
+            outs.append(bp.finalize().view(-1)[::97].cpu())
+    assert torch.equal(outs[0], outs[1])
 
 
 def test_reciprocal_modes_accuracy_table():

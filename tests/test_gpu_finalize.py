@@ -98,7 +98,10 @@ def test_fused_call_on_a_slab_and_with_no_images():
         empty = destination("device", (20, vol.L, vol.L))
         bp.add_projections_finalize(qh[:0], A[:0], empty)
         assert torch.equal(empty.cpu(), ref)
-    assert rel_l2(out.numpy(), whole[8:28].numpy()) <= 1e-6
+    # the slab's bricks need not line up with the cube's, so per-brick
+    # centring rounds each differently: two float32 results, each within
+    # about 1e-6 of the exact sums
+    assert rel_l2(out.numpy(), whole[8:28].numpy()) <= 2.5e-6
 
 
 def test_fused_call_rejects_a_null_output():

@@ -21,9 +21,11 @@ def learned():
 
 
 def test_backproject_function_gradcheck():
-    """32^3 with 12 projections of 64 x 48.  The map is linear, so central
-    differences are exact up to float32 rounding of the outputs; fast mode
-    compares v^T J u from finite differences with v^T (J u) from backward."""
+    """The float32 product kernels at 32^3 with 12 projections of 64 x 48.
+    The map is linear, so central differences are exact up to float32
+    rounding of the outputs; fast mode compares v^T J u from finite
+    differences with v^T (J u) from backward.  (The float64 gradcheck below
+    checks the same map with gradcheck's defaults.)"""
     lm, api = learned(), native()
     scan, vol = synth.SCANS["grad"], synth.Volume(32)
     A = oracle.carm_matrices(scan)
@@ -32,6 +34,55 @@ def test_backproject_function_gradcheck():
     assert torch.autograd.gradcheck(lambda x: lm.backproject(x, bp, A), (p,), eps=0.5, atol=2e-4,
                                     rtol=2e-3, fast_mode=True, nondet_tol=1e-5)
     bp.close()
+
+
+def f64_operator(scan, vol):
+    from paper_1104_5243_gb300 import _f64
+    from paper_1104_5243_gb300 import build as B
+    native()
+    B.build_f64()
+    return _f64.DirectF64(vol.L, vol.R, vol.O, scan.isx, scan.isy)
+
+
+def test_float64_direct_kernels_match_the_oracle():
+    """The double instantiations of the direct backprojection and direct
+    adjoint kernels (test-support library) against the FP64 oracle on the
+    gradcheck geometry: both sides compute in float64, so they agree to
+    rounding order (1e-12), which pins the kernels' geometry, indexing and
+    zero padding far below float32 resolution."""
+    scan, vol = synth.SCANS["grad"], synth.Volume(32)
+    A = oracle.carm_matrices(scan)
+    op = f64_operator(scan, vol)
+    rng = np.random.default_rng(5)
+    # the oracle reads float32 images: both sides get the same values
+    p = rng.standard_normal((scan.n, scan.isy, scan.isx)).astype(np.float32)
+    f = rng.standard_normal((vol.L,) * 3)
+    ref = oracle.backproject(vol.L, vol.R, vol.O, p, A)
+    op.reset()
+    op.add_projections(torch.from_numpy(p.astype(np.float64)).cuda(), A)
+    got = op.finalize().cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-12
+    adj = op.adjoint(torch.from_numpy(f).cuda(), A).cpu().numpy()
+    aref = oracle.adjoint(vol.L, vol.R, vol.O, f, A, scan.isx, scan.isy)
+    aabs = oracle.adjoint(vol.L, vol.R, vol.O, np.abs(f), A, scan.isx, scan.isy)
+    assert np.linalg.norm(adj - aref) / np.linalg.norm(aabs) <= 1e-12
+
+
+def test_backproject_function_gradcheck_float64():
+    """gradcheck in float64 at 32^3 with 12 projections of 64 x 48, the full
+    Jacobian (36864 inputs x 32768 outputs, not fast mode) with gradcheck's
+    default step (1e-6) and tolerances (atol 1e-5, rtol 1e-3): the forward is
+    the float64 direct backprojection, the backward the float64 direct
+    adjoint (the double instantiation of the library's adjoint kernel),
+    through the same autograd Function as the float32 path."""
+    lm = learned()
+    scan, vol = synth.SCANS["grad"], synth.Volume(32)
+    A = oracle.carm_matrices(scan)
+    op = f64_operator(scan, vol)
+    torch.manual_seed(0)
+    p = torch.randn((scan.n, scan.isy, scan.isx), dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda x: lm.backproject(x, op, A), (p,), fast_mode=False)
+    torch.cuda.empty_cache()
 
 
 def test_row_filter_function_gradcheck():
