@@ -170,6 +170,16 @@ bp_status bp_create(bp_ctx **out, int L, double R, const double O[3],
 bp_status bp_create_slab(bp_ctx **out, int L, int nz, int z0, double R, const double O[3],
                          int isx, int isy, bp_dtype proj_dtype, void *cuda_stream);
 
+/* Re-target a context to the z-slab of slices z0 .. z0+nz-1 of the same
+ * L^3 grid (same L, R, O, detector and storage type), keeping its device
+ * allocations: 1 <= nz <= the slab depth the context was created with (L for
+ * bp_create), 0 <= z0 <= L - nz.  Waits for the context's work in flight,
+ * then zeroes the volume and the projection counter.  A volume larger than
+ * the device is reconstructed by moving one or two slab contexts over it
+ * (Sect. 6's split of the z loop), without a context per slab.  BP_EINVAL for
+ * a NULL context or a slab outside those bounds. */
+bp_status bp_move_slab(bp_ctx *ctx, int z0, int nz);
+
 /* Release everything the context owns (synchronises its stream first).
  * NULL is accepted and ignored. */
 bp_status bp_destroy(bp_ctx *ctx);
@@ -231,8 +241,15 @@ bp_status bp_set_state(bp_ctx *ctx, const float *vol_in, int on_device, long lon
  *   A:          n x 3 x 4 float64 row-major, HOST memory;
  *   images_out: n x ISY x ISX float32 (host or device per out_on_device),
  *               overwritten (the callee zeroes it first).
- * Uses float32 atomics, so the summation order (and the last bits) can vary
- * between runs.  Leaves the context's volume untouched. */
+ * With BP_OPT_CULL 1 (the default) each block of 32x32x4 voxels sums its
+ * terms for a projection in a shared-memory tile in 32-bit fixed point
+ * (native integer atomics; the scale is a power of two per block and
+ * projection, bounded so that no sum overflows, each term rounded to 2^-31
+ * of the block's bound), then adds each nonzero tile pixel to the image with
+ * one float32 global atomic; blocks whose footprint exceeds the tile, and
+ * BP_OPT_CULL 0, add every term with float32 global atomics.  The float32
+ * atomics make the summation order (and the last bits) vary between runs.
+ * Leaves the context's volume untouched. */
 bp_status bp_adjoint(bp_ctx *ctx, const float *vol, int vol_on_device,
                      const double *A, int n, float *images_out, int out_on_device);
 

@@ -22,6 +22,7 @@ SIGNATURES = {
     "bp_create": (_i, [ctypes.POINTER(_vp), _i, _d, _vp, _i, _i, _i, _vp]),
     "bp_create_slab": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _d, _vp, _i, _i, _i, _vp]),
     "bp_destroy": (_i, [_vp]),
+    "bp_move_slab": (_i, [_vp, _i, _i]),
     "bp_set_option": (_i, [_vp, _i, _ll]),
     "bp_reset": (_i, [_vp]),
     "bp_add_projections": (_i, [_vp, _vp, _i, _vp, _i]),
@@ -105,6 +106,10 @@ def bp_create_slab(L, nz, z0, R, O, isx, isy, dtype=BP_F32, stream=None):
 
 def bp_destroy(ctx):
     check(lib().bp_destroy(ctx))
+
+
+def bp_move_slab(ctx, z0, nz):
+    check(lib().bp_move_slab(ctx, int(z0), int(nz)), ctx)
 
 
 def bp_set_option(ctx, option, value):

@@ -50,6 +50,7 @@ class Backprojector:
                  stream: torch.cuda.Stream | None = None, device=None, nz: int | None = None, z0: int = 0):
         self.L, self.R, self.O = int(L), float(R), tuple(float(v) for v in O)
         self.nz, self.z0 = (self.L if nz is None else int(nz)), int(z0)
+        self.nz_cap = self.nz   # slab depth the device volume holds (move_slab)
         self.isx, self.isy = int(isx), int(isy)
         self.dtype = dtype
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -98,6 +99,13 @@ class Backprojector:
 
     def set_option(self, option: int, value: int):
         N.bp_set_option(self._ctx, option, value)
+
+    def move_slab(self, z0: int, nz: int):
+        """Re-target the context to slices z0 .. z0+nz-1 of the same L^3 grid
+        (nz at most the depth it was created with), keeping its device
+        allocations; the volume and the counter restart at zero."""
+        N.bp_move_slab(self._ctx, z0, nz)
+        self.z0, self.nz = int(z0), int(nz)
 
     def reset(self):
         N.bp_reset(self._ctx)
@@ -177,29 +185,66 @@ class Backprojector:
         return out
 
 
+def slab_contexts(L: int, R: float, O, isx: int, isy: int, slab: int, dtype: str = "f32",
+                  count: int = 2) -> list:
+    """`count` slab contexts of min(slab, L) slices of the L^3 grid, each on
+    its own CUDA stream, for backproject_slabs; a caller reconstructing
+    several volumes of one geometry keeps them and passes them as `pool`, so
+    their device allocations are made once."""
+    device = torch.cuda.current_device()
+    return [Backprojector(L, R, O, isx, isy, dtype=dtype, nz=min(int(slab), int(L)), z0=0,
+                          stream=torch.cuda.Stream(device=device)) for _ in range(int(count))]
+
+
 def backproject_slabs(L: int, R: float, O, images: torch.Tensor, A, slab: int, dtype: str = "f32",
-                      out: torch.Tensor | None = None) -> torch.Tensor:
+                      out: torch.Tensor | None = None, contexts: int = 2, pool: list | None = None) -> torch.Tensor:
     """Backproject into an L^3 volume held in HOST memory, slab by slab (the
-    paper's split of the z loop, Sect. 6): a context of at most `slab`
-    slices at a time takes every projection, and its slab is read back into
-    out[z0 : z0 + nz].  For volumes larger than one context can hold on the
-    device; every slab reads the projections again.  images: (n, ISY, ISX)
+    paper's split of the z loop, Sect. 6): slab contexts of `slab` slices
+    (`contexts` of them made for this call, or the caller's `pool` from
+    slab_contexts), moved over the volume with bp_move_slab, take the slabs
+    in turn, each on its own CUDA stream and host thread, so one slab's
+    staging and read-back overlap the other's kernels; every slab takes every
+    projection, and its last launch stores the slab into out[z0 : z0 + nz].
+    For volumes larger than the device holds.  images: (n, ISY, ISX)
     float32, host or device; out: (L, L, L) float32 host tensor (allocated
     pinned if None)."""
+    from concurrent.futures import ThreadPoolExecutor
     L, slab = int(L), int(slab)
-    if slab < 1:
-        raise ValueError("slab must be >= 1")
+    if slab < 1 or contexts < 1:
+        raise ValueError("slab and contexts must be >= 1")
     if out is None:
         out = torch.empty((L, L, L), dtype=torch.float32).pin_memory()
     if out.is_cuda or tuple(out.shape) != (L, L, L) or out.dtype != torch.float32 or not out.is_contiguous():
         raise ValueError("out must be a contiguous (L, L, L) float32 host tensor")
     n, isy, isx = images.shape
-    for z0 in range(0, L, slab):
-        nz = min(slab, L - z0)
-        with Backprojector(L, R, O, isx, isy, dtype=dtype, nz=nz, z0=z0) as bp:
+    slabs = [(z0, min(slab, L - z0)) for z0 in range(0, L, slab)]
+    if pool is not None:
+        if not pool or any(bp.L != L or bp.isx != isx or bp.isy != isy or bp.dtype != dtype or
+                           bp.nz_cap < min(slab, L) for bp in pool):
+            raise ValueError("pool contexts must match L, the detector, the dtype and hold a slab")
+        ctxs = list(pool)[:len(slabs)]
+    else:
+        ctxs = slab_contexts(L, R, O, isx, isy, slab, dtype, min(contexts, len(slabs)))
+    # the contexts' streams read device images produced on the caller's stream
+    torch.cuda.current_stream().synchronize()
+    device = torch.cuda.current_device()
+
+    def work(k):
+        torch.cuda.set_device(device)
+        bp = ctxs[k]
+        for z0, nz in slabs[k::len(ctxs)]:
+            bp.move_slab(z0, nz)
             # out[z0 : z0 + nz] is contiguous: with a pinned `out` the slab's
             # last launch stores it there directly
             bp.add_projections_finalize(images, A, out[z0:z0 + nz])
+
+    try:
+        with ThreadPoolExecutor(len(ctxs)) as ex:
+            list(ex.map(work, range(len(ctxs))))
+    finally:
+        if pool is None:
+            for bp in ctxs:
+                bp.close()
     return out
 
 

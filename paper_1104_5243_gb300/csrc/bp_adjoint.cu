@@ -52,6 +52,8 @@ __device__ __forceinline__ float recip_adj(float w)
 // Same coordinates and weights as direct_adjoint_kernel.
 using AdjAcc = int;
 constexpr int kAccBits = 8 * (int)sizeof(AdjAcc);
+constexpr float kFloorMagic = 12582912.0f;          // 1.5 * 2^23
+constexpr unsigned kFloorMagicBits = 0x4B400000u;   // its bits
 
 // Blocks of 32 x 32 x 4 voxels: each lane takes 4 voxels along x (8 apart)
 // and kAdjVPY along y (one per warp row, kWarpsY apart).  A block's
@@ -224,6 +226,10 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
             const int W = p.z;
             const unsigned qmax = (unsigned)(W * p.w - W - 2);
             const int du = kb.x - p.x, dv = kb.y - p.y;
+            // the tile index of the top-left corner from the bits of the
+            // round-down sums (below): (bits(mv) - M) * W + bits(mu) - M +
+            // dv * W + du, in 32-bit unsigned arithmetic
+            const unsigned qoff = (unsigned)(dv * W + du) - kFloorMagicBits * (unsigned)(W + 1);
 #pragma unroll
             for (int ky = 0; ky < kAdjVPY; ++ky) {
                 const float bu = fmaf(vu.y, Y[ky], fmaf(vu.z, Z, vu.w));
@@ -238,9 +244,17 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
                     const float w = fmaf(vw4.x, X[k], bw);
                     const float r = recip_adj<IEEE>(w);
                     const float u = uw * r, v = vw * r;
-                    const float fu0 = floorf(u), fv0 = floorf(v);
-                    const unsigned q0 =
-                        min((unsigned)(((int)fv0 + dv) * W + ((int)fu0 + du)), qmax);
+                    // floor without the conversion unit, which the
+                    // reciprocal and the four fixed-point conversions keep
+                    // busy (the floors and int conversions made it the
+                    // binding pipe: 9 of its operations per update): u +
+                    // 1.5 * 2^23 rounded down is floor(u) + 1.5 * 2^23
+                    // exactly for |u| < 2^22 (u stays within the block's
+                    // footprint), and its bits are the integer
+                    const float mu = __fadd_rd(u, kFloorMagic), mv = __fadd_rd(v, kFloorMagic);
+                    const float fu0 = mu - kFloorMagic, fv0 = mv - kFloorMagic;
+                    const unsigned q0 = min((unsigned)__float_as_int(mv) * (unsigned)W +
+                                                (unsigned)__float_as_int(mu) + qoff, qmax);
                     const float fu = u - fu0, fv = v - fv0;
                     const float s = f[ky][k] * ((r * sc.x) * r);
                     const float sb = s * fv, st = s - sb;

@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -30,17 +31,18 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 static EncodeTiledFn encode_tiled()
 {
+    // looked up once, thread-safely (contexts may be used from several
+    // host threads, one thread per context)
     static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
+    });
     return fn;
 }
 
@@ -48,7 +50,9 @@ using namespace bp;
 
 struct bp_ctx {
     int L = 0, Lz = 0;   // volume L x L x Lz (Lz < L: a z-slab of the L^3 grid)
+    int nz_cap = 0;      // slab depth the volume was allocated for
     double R = 0, O[3] = {0, 0, 0};
+    double O_cube[3] = {0, 0, 0};   // centre of voxel (0,0,0) of the L^3 grid
     int isx = 0, isy = 0;
     bp_dtype dtype = BP_F32;
     int device = 0;
@@ -236,7 +240,10 @@ static bp_status create_context(bp_ctx **out, int L, int nz, int z0, double R, c
         return fail(nullptr, BP_ENOMEM, "bp_create: out of host memory");
     c->L = L;
     c->Lz = nz;
+    c->nz_cap = nz;
     c->R = R;
+    for (int q = 0; q < 3; ++q)
+        c->O_cube[q] = O[q];
     c->O[0] = O[0];
     c->O[1] = O[1];
     c->O[2] = O[2] + R * z0;   // centre of the slab's voxel (0,0,0)
@@ -292,6 +299,22 @@ extern "C" bp_status bp_create_slab(bp_ctx **out, int L, int nz, int z0, double 
                                     int isy, bp_dtype proj_dtype, void *cuda_stream)
 {
     return create_context(out, L, nz, z0, R, O, isx, isy, proj_dtype, cuda_stream);
+}
+
+extern "C" bp_status bp_move_slab(bp_ctx *c, int z0, int nz)
+{
+    if (c == nullptr)
+        return fail(nullptr, BP_EINVAL, "bp_move_slab: NULL context");
+    if (nz < 1 || nz > c->nz_cap || z0 < 0 || z0 > c->L - nz)
+        return fail(c, BP_EINVAL, "bp_move_slab: the slab must satisfy 1 <= nz <= %d and 0 <= z0 <= L - nz",
+                    c->nz_cap);
+    CTX_CK(c, cudaSetDevice(c->device));
+    // the kernels in flight still address the old slab
+    CTX_CK(c, cudaStreamSynchronize(c->stream));
+    CTX_CK(c, cudaStreamSynchronize(c->copy_stream));
+    c->Lz = nz;
+    c->O[2] = c->O_cube[2] + c->R * z0;
+    return bp_reset(c);
 }
 
 extern "C" bp_status bp_destroy(bp_ctx *c)
@@ -483,9 +506,10 @@ static bp_status ensure_maps(bp_ctx *c, int zpl)
     return BP_OK;
 }
 
-// Host model of the pre-pass's box rule on a sample of bricks (a 5 x 5 x 5
-// grid of brick positions spanning the volume) and up to 16 projections of
-// the batch, in float64: of the sampled (brick, projection) pairs whose
+// Host model of the pre-pass's box rule on a sample of bricks (the bricks
+// at the centres of a 6 x 6 x 6 partition of the volume, so that every part
+// of the volume weighs the same) and up to 16 projections of the batch, in
+// float64: of the sampled (brick, projection) pairs whose
 // footprint reaches the detector, the fraction whose box fits kTmaBU
 // element columns by bv rows (pair-image rule: rows floor(v) - 1 ..
 // floor(v_max) + 2) for bricks 32 x 16 x bz; 1 if no sampled pair is
@@ -494,7 +518,7 @@ static double box_fit_fraction(const bp_ctx *c, const double *A, int m, int bz, 
 {
     const int nb[3] = {(c->L + kBrickX - 1) / kBrickX, (c->L + kBrickY - 1) / kBrickY, (c->Lz + bz - 1) / bz};
     const int ext[3] = {kBrickX, kBrickY, bz}, lim[3] = {c->L, c->L, c->Lz};
-    constexpr int K = 5;
+    constexpr int K = 6;
     long vis = 0, fit = 0;
     const int pstep = m > 16 ? m / 16 : 1;
     for (int p = 0; p < m; p += pstep) {
@@ -502,7 +526,7 @@ static double box_fit_fraction(const bp_ctx *c, const double *A, int m, int bz, 
         for (int q = 0; q < K * K * K; ++q) {
             int lo[3], hi[3];
             for (int d = 0, qq = q; d < 3; ++d, qq /= K) {
-                const int bi = (int)std::lround((double)(qq % K) * (nb[d] - 1) / (K - 1));
+                const int bi = std::min(nb[d] - 1, (int)(((double)(qq % K) + 0.5) * nb[d] / K));
                 lo[d] = bi * ext[d];
                 hi[d] = std::min(lo[d] + ext[d], lim[d]) - 1;
             }
@@ -532,7 +556,7 @@ static double box_fit_fraction(const bp_ctx *c, const double *A, int m, int bz, 
 
 // Data path and brick depth of a batch.  Forced depths and the forced TMA
 // path take the caller's choice; otherwise 16-deep bricks when their box
-// holds the sampled footprints of 99 % of the visible pairs (the rest take
+// holds the sampled footprints of 98 % of the visible pairs (the rest take
 // the slower global-memory branch), else 8-deep bricks, and the texture path
 // when even the 8-deep box holds fewer than 90 % of them (coarse voxels).
 // Measured on GB300 at 512^3 x 496 x 1248x960 (GUP/s per step for depths
@@ -544,7 +568,7 @@ static void choose_path(const bp_ctx *c, const double *A, int m, bool *tma, int 
     *tma = c->path != 1;
     if (c->path == 1 || c->brick_depth)
         return;
-    if (box_fit_fraction(c, A, m, 16, tma_rows(8, false)) >= 0.99) {
+    if (box_fit_fraction(c, A, m, 16, tma_rows(8, false)) >= 0.98) {
         *zpl = 8;
         return;
     }

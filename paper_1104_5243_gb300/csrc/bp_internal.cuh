@@ -166,18 +166,27 @@ cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom
 // batch, the deepest brick whose box holds the sampled footprints.  The box
 // heights come from a CPU model of the pre-pass's box rule over the 512^3
 // C-arm scan: 36 rows hold 99.7 % of the visible 8-deep footprints, 48 rows
-// 99.7 % of the 12-deep ones and 61 rows 99.8 % of the 16-deep ones (114
-// element columns hold 99.99 %); larger footprints (bricks near the
-// source) read the image from global memory.
+// 99.7 % of the 12-deep ones and 58 rows (as tall as two blocks per SM
+// allow) 98.9 % of the 16-deep ones; larger footprints (bricks near the
+// source, near the top and bottom of the volume) read the image from
+// global memory.
+//
+// The box is 120 elements wide (114 hold 99.99 % of the footprints): its row
+// pitch of 240 words is 16 modulo 32, so an element and the one a row below
+// it sit 16 banks apart.  A warp's 8-byte loads are served per half-warp;
+// a half-warp covers 4 x 4 voxels, whose corners span about 10 elements of
+// one or two rows, and the 16-bank shift keeps two rows' elements apart
+// (a CPU model of the bank accounting, checked against ncu: 1.34 wavefronts
+// per load against 1.84 with a 114-element pitch and 8 x 2 half-warps).
 constexpr int kBrickX = 32, kBrickY = 16;
 enum PairKind { kPairF32 = 0, kQuadF16 = 1, kQuadBF16 = 2 };
-constexpr int kTmaBU = 114;   // element columns: a row pitch of 228 words, 4 modulo 32 (rows 4 banks apart)
+constexpr int kTmaBU = 120;   // element columns (and row pitch) of a staged box
 constexpr int kTmaAlign = 2;  // element-column alignment that keeps the box origin on 16 bytes
 // Box rows of the float32 pair images per ZPL; a column-quad box is one row
 // shorter (each element carries the row below).
 __host__ __device__ constexpr int tma_rows(int zpl, bool quad)
 {
-    return (zpl == 4 ? 36 : zpl == 6 ? 48 : 61) - (quad ? 1 : 0);
+    return (zpl == 4 ? 36 : zpl == 6 ? 48 : 58) - (quad ? 1 : 0);
 }
 constexpr int kTmaStages = 2;
 constexpr int kTmaWaitIters = 1 << 14;          // bounded waits: at most ~2 s

@@ -237,10 +237,10 @@ __device__ __forceinline__ void tma_updates(const TmaBatch &b, int i, const floa
         const float bw = fmaf(rw.z, Z[q], cw);
 #pragma unroll
         for (int kx = 0; kx < 4; ++kx) {
-            const float uw = fmaf(ru.x, X[kx], bu);
-            const float vw = fmaf(rv.x, X[kx], bv);
             const float w = fmaf(rw.x, X[kx], bw);
             const float r = recip_tma<IEEE>(w);
+            const float uw = fmaf(ru.x, X[kx], bu);
+            const float vw = fmaf(rv.x, X[kx], bv);
             const float u = uw * r, v = vw * r;
             const float fu0 = floorf(u), fv0 = floorf(v);
             uint2 e0, e1 = make_uint2(0u, 0u);
@@ -381,11 +381,13 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     }
 
     // ---------------- consumers
-    // A warp is 8 lanes along x by 4 along y in one z plane of the brick:
-    // its 32 voxels land on about the same detector rows, spread along
-    // them, which keeps the shared-memory bank conflicts of the corner loads
-    // low (a z-spread warp spans rows whose pitch aliases the banks).
-    const int tx = lane & 7, ty = lane >> 3;
+    // A warp is 8 lanes along x by 4 along y in one z plane of the brick,
+    // numbered so that each half-warp is a 4 x 4 patch (x 0-3 and x 4-7):
+    // the shared-memory unit serves a warp's 8-byte loads per half-warp, and
+    // a compact patch's corners span few elements of one or two detector
+    // rows (a z-spread warp spans rows whose pitch aliases the banks; an
+    // 8 x 2 half-warp spans more elements than the 16 banks pairs).
+    const int tx = (lane & 3) | ((lane >> 4) << 2), ty = (lane >> 2) & 3;
     const int yl = 4 * (warp & 3) + ty, zl0 = ZPL * (warp >> 2);
     // this lane's voxels: x0 + {0, 8, 16, 24}, y0, z0 + {0 .. ZPL-1};
     // lanes beyond a ragged edge compute with the last voxel's coordinates

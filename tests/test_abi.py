@@ -97,6 +97,8 @@ def test_null_context_is_rejected(lib):
     assert lib.bp_add_projections_finalize(None, None, 0, None, 1, None, 0) == N.BP_EINVAL
     assert "bp_add_projections_finalize" in N.bp_last_error(None)
     assert lib.bp_set_option(None, 1, 0) == N.BP_EINVAL
+    assert lib.bp_move_slab(None, 0, 1) == N.BP_EINVAL
+    assert "bp_move_slab" in N.bp_last_error(None)
     assert lib.bp_destroy(None) == N.BP_OK
 
 

@@ -41,8 +41,13 @@ def test_tiny_phantom_fp32_matches_oracle():
     scan, vol, A, ell, q, ref = tiny_phantom_case()
     got = run_gpu(vol, scan, A, q)
     err = rel_l2(got, ref)
-    print(f"tiny fp32 rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e} PSNR {oracle.psnr(got, ref):.1f} dB")
+    mabs = float(np.abs(got - ref).max() / np.abs(ref).max())
+    print(f"tiny fp32 rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e} (relative {mabs:.3e}) "
+          f"PSNR {oracle.psnr(got, ref):.1f} dB")
     assert err <= FP32_TOL
+    # ramp-filtered data mixes signs: single voxels may carry more of the
+    # error than the rel-L2 shows, so the max-abs bar is 4x the rel-L2 bar
+    assert mabs <= 4 * FP32_TOL
 
 
 @pytest.mark.parametrize("dtype,tol", [("f16", FP16_TOL), ("bf16", BF16_TOL)])
@@ -50,8 +55,10 @@ def test_tiny_phantom_16bit_storage(dtype, tol):
     scan, vol, A, ell, q, ref = tiny_phantom_case()
     got = run_gpu(vol, scan, A, q, dtype=dtype)
     err = rel_l2(got, ref)
-    print(f"tiny {dtype} rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e} PSNR {oracle.psnr(got, ref):.1f} dB")
-    assert err <= tol
+    mabs = float(np.abs(got - ref).max() / np.abs(ref).max())
+    print(f"tiny {dtype} rel-L2 {err:.3e} max-abs {np.abs(got - ref).max():.3e} (relative {mabs:.3e}) "
+          f"PSNR {oracle.psnr(got, ref):.1f} dB")
+    assert err <= tol and mabs <= 4 * tol
 
 
 def test_ieee_reciprocal_option():
@@ -180,9 +187,13 @@ def test_full_size_sampled_voxels(L, dtype, tol):
     ref = oracle.backproject_voxels(vol.L, vol.R, vol.O, stack, A, idx)
     g = got[torch.from_numpy(idx).cuda()].cpu().numpy()
     err = rel_l2(g, ref)
+    mabs = float(np.abs(g - ref).max() / np.abs(ref).max())
     print(f"{L}^3 {dtype} sampled rel-L2 {err:.3e} max-abs {np.abs(g - ref).max():.3e} "
-          f"(max |ref| {np.abs(ref).max():.3e})")
+          f"(max |ref| {np.abs(ref).max():.3e}, relative {mabs:.3e})")
     assert err <= tol
+    # the largest single-voxel error, relative to the largest value: within
+    # the same bar as the rel-L2 (a voxel sums 496 rounded terms of one sign)
+    assert mabs <= tol
     bp.close()
 
 
@@ -211,8 +222,9 @@ def test_largest_and_ragged_volumes_sampled(L, dtype, tol):
     del out
     torch.cuda.empty_cache()
     err = rel_l2(g, ref)
-    print(f"{L}^3 {dtype} from {len(A)} projections: sampled rel-L2 {err:.3e}")
-    assert err <= tol
+    mabs = float(np.abs(g - ref).max() / np.abs(ref).max())
+    print(f"{L}^3 {dtype} from {len(A)} projections: sampled rel-L2 {err:.3e}, max-abs relative {mabs:.3e}")
+    assert err <= tol and mabs <= tol
 
 
 @pytest.mark.parametrize("path", [1, 2])
@@ -248,8 +260,13 @@ def test_full_detector_ramp_filtered_phantom(dtype, tol, path):
         bp.close()
         g = got[torch.from_numpy(idx).cuda()].cpu().numpy()
         errs[centre] = rel_l2(g, ref)
+        mabs = float(np.abs(g - ref).max() / np.abs(ref).max())
         print(f"512^3 phantom {dtype} path={path} block_centre={centre} sampled rel-L2 {errs[centre]:.3e} "
-              f"max-abs {np.abs(g - ref).max():.3e}")
+              f"max-abs {np.abs(g - ref).max():.3e} (relative {mabs:.3e})")
+        if centre == 1:
+            # ramp-filtered data mixes signs, so single voxels can carry a
+            # larger share of the error than the rel-L2 shows: 4x the bar
+            assert mabs <= 4 * tol
     assert errs[1] <= tol
     if dtype == "f32":
         # centring per block instead of per projection: u', v' stay within a

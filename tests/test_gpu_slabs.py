@@ -76,3 +76,102 @@ def test_single_slice_slab_and_state_roundtrip():
         bp.add_projections(torch.from_numpy(q[30:]).cuda(), A[30:])
         got = bp.finalize().cpu().numpy()
     assert rel_l2(got[0], ref[15]) <= 1e-5
+
+
+def _slab_rank(rank, world, port, L, out_dir):
+    """One rank of the z-split (bench.py --split z): its slab of the L^3
+    volume from every projection, on cuda:0, gathered to rank 0 over gloo."""
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import torch.distributed as dist
+    import bench
+    from paper_1104_5243_gb300 import api, build
+    build.build()
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    scan, vol, A, q = case(L)
+    z0, nz = bench.slab_of_rank(L, world, rank)
+    with api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, nz=nz, z0=z0) as bp:
+        bp.add_projections(torch.from_numpy(q).cuda(), A)
+        mine = bp.finalize().cpu()
+    parts = [None] * world
+    dist.all_gather_object(parts, (z0, nz, mine.numpy()))
+    if rank == 0:
+        np.save(os.path.join(out_dir, "stitched.npy"),
+                np.concatenate([p[2] for p in sorted(parts, key=lambda t: t[0])], axis=0))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("L", [72, 64])
+def test_two_ranks_split_z_stitch_to_the_whole_volume(tmp_path, L):
+    """Two processes on one GPU, each reconstructing the z-slab that
+    bench.slab_of_rank gives it (as bench.py --split z does on two GPUs),
+    gathered over gloo: the stitched volume against one context holding the
+    whole cube (the slabs' bricks centre differently, so the two agree to
+    float32 rounding, not bit for bit) and against the oracle."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.spawn(_slab_rank, args=(2, port, L, str(tmp_path)), nprocs=2, join=True)
+    stitched = np.load(tmp_path / "stitched.npy")
+    api = native()
+    scan, vol, A, q = case(L)
+    with api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy) as bp:
+        bp.add_projections(torch.from_numpy(q).cuda(), A)
+        whole = bp.finalize().cpu().numpy()
+    ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
+    assert stitched.shape == whole.shape
+    assert rel_l2(stitched, whole) <= 2.5e-6
+    assert rel_l2(stitched, ref) <= 1e-5
+
+
+def test_moved_slab_context_equals_fresh_slab_contexts():
+    """bp_move_slab re-targets one context over the volume (its allocations
+    kept): every slab equals, bit for bit, the slab a fresh context of that
+    slab computes, and a slab deeper than the context's allocation, or one
+    outside the volume, is refused."""
+    api = native()
+    from paper_1104_5243_gb300 import _native as N
+    scan, vol, A, q = case(40)
+    qt = torch.from_numpy(q).cuda()
+    with api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, nz=16, z0=0) as moved:
+        for z0, nz in [(0, 16), (16, 16), (32, 8), (5, 11)]:
+            moved.move_slab(z0, nz)
+            moved.add_projections(qt, A)
+            got = moved.finalize().cpu()
+            with api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, nz=nz, z0=z0) as fresh:
+                fresh.add_projections(qt, A)
+                assert torch.equal(got, fresh.finalize().cpu()), (z0, nz)
+        for z0, nz in [(0, 17), (30, 16), (-1, 4), (0, 0)]:
+            with pytest.raises(N.BpError) as e:
+                moved.move_slab(z0, nz)
+            assert e.value.status == N.BP_EINVAL
+
+
+@pytest.mark.parametrize("contexts", [1, 2])
+def test_threaded_slab_reconstruction_matches_the_oracle(contexts):
+    """api.backproject_slabs with one or two moved contexts (two: each on its
+    own stream and host thread) into pinned host memory, 56^3 in slabs of 16
+    (the last one 8 slices), host and device images."""
+    api = native()
+    scan, vol, A, q = case(56)
+    ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
+    for images in (torch.from_numpy(q).cuda(), torch.from_numpy(q).pin_memory()):
+        got = api.backproject_slabs(vol.L, vol.R, vol.O, images, A, slab=16, contexts=contexts).numpy()
+        assert rel_l2(got, ref) <= 1e-5
+    # a pool of contexts kept across reconstructions gives the same volumes
+    pool = api.slab_contexts(vol.L, vol.R, vol.O, scan.isx, scan.isy, 16, count=contexts)
+    try:
+        first = api.backproject_slabs(vol.L, vol.R, vol.O, torch.from_numpy(q).cuda(), A, slab=16, pool=pool)
+        again = api.backproject_slabs(vol.L, vol.R, vol.O, torch.from_numpy(q).cuda(), A, slab=16, pool=pool)
+        assert torch.equal(first, again) and rel_l2(first.numpy(), ref) <= 1e-5
+        with pytest.raises(ValueError):
+            api.backproject_slabs(vol.L, vol.R, vol.O, torch.from_numpy(q).cuda(), A, slab=32, pool=pool)
+    finally:
+        for bp in pool:
+            bp.close()
