@@ -62,8 +62,7 @@ TEXELS_PER_UPDATE = 4
 # profiles/<kernel>_<form>_512x64.md), and shared-memory bandwidth including
 # the TMA fill of each brick's box.
 ISSUE_PER_SM_CLK = 128.0
-INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 28.5, ("tma", "f16"): 32.4,
-                    ("tma", "bf16"): 32.4}
+INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 26.3, ("tma", "f16"): 25.2}
 # Adjoint (B^T, the same arithmetic per update as B, with the four corner
 # terms scattered instead of gathered):
 #   fp32_pipe: the forward's 20.5 FP32-pipe operations (geometry, floor,
@@ -74,8 +73,8 @@ INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", 
 # Diagnostics: ncu's instructions per update and wavefronts per atomic
 # instruction (profiles/bp_adjoint_smem_kernel_256.md).
 ADJ_ATOMICS_PER_UPDATE = 4
-ADJ_INSTR_PER_UPDATE = 50.0
-ADJ_ATOMIC_WAVEFRONTS = 3.7
+ADJ_INSTR_PER_UPDATE = 49.9
+ADJ_ATOMIC_WAVEFRONTS = 3.69
 
 
 def adjoint_roofline_gups(sm_mhz: float, sms: int) -> dict:
@@ -102,11 +101,14 @@ def texel_bytes_per_update(form: str) -> float:
     return TEXELS_PER_UPDATE * (4 if form == "f32" else 2)
 
 
-def tma_smem_bytes_per_update(form: str) -> float:
-    """Shared-memory bytes per update of the TMA kernel as built (two pair
-    loads plus the box fill per 32 x 16 x 8 brick); a diagnostic."""
-    pair, bu = (8, 114) if form == "f32" else (4, 100)
-    return 2.0 * pair + bu * 36 * pair / (32 * 16 * 8)
+def tma_smem_bytes_per_update(form: str, depth: int = 16) -> float:
+    """Shared-memory bytes per update of the TMA kernel as built: the staged
+    8-byte elements an update loads (two for float32 pairs, one for 16-bit
+    column quads) plus the box fill (120 element columns by the box rows of
+    the brick depth) per 32 x 16 x depth brick; a diagnostic."""
+    rows = {8: 36, 12: 48, 16: 58}[depth] - (0 if form == "f32" else 1)
+    loads = 2 if form == "f32" else 1
+    return 8.0 * loads + 120 * rows * 8 / (32 * 16 * depth)
 
 
 def roofline_peak_gups(path: str, form: str, sm_mhz: float, sms: int, gather_per_sm_clk: float) -> dict:
@@ -123,7 +125,7 @@ def roofline_peak_gups(path: str, form: str, sm_mhz: float, sms: int, gather_per
     return bounds
 
 
-def roofline_diagnostics_gups(path: str, form: str, sm_mhz: float, sms: int) -> dict:
+def roofline_diagnostics_gups(path: str, form: str, sm_mhz: float, sms: int, depth: int = 16) -> dict:
     """What the kernel as built is limited by (from its ncu profile): issue at
     its measured instructions per update, and for the TMA path shared-memory
     bandwidth including the box fill.  Explains a fraction; not the peak."""
@@ -134,25 +136,27 @@ def roofline_diagnostics_gups(path: str, form: str, sm_mhz: float, sms: int) -> 
         d["issue_at_measured_instr"] = sms * ISSUE_PER_SM_CLK / instr * f / 1e9
         d["instr_per_update"] = instr
     if path == "tma":
-        d["smem_with_box_fill"] = sms * SMEM_BYTES_PER_SM_CLK / tma_smem_bytes_per_update(form) * f / 1e9
+        d["smem_with_box_fill"] = sms * SMEM_BYTES_PER_SM_CLK / tma_smem_bytes_per_update(form, depth) * f / 1e9
     return d
 
 
 def algorithmic_bytes(L: int, n: int, isx: int, isy: int, form: str, path: str, computed_fraction: float,
-                       Lz: int | None = None) -> int:
+                       Lz: int | None = None, depth: int = 16) -> int:
     """Bytes one mid-step launch of the backprojection kernel must move: the
     L x L x Lz volume (Lz = L for the whole cube) read and written once, each
-    of the n projections read once (the TMA path reads pair images: two pixels per element, row pitch padded to
-    16 B), and for the FP32 form the per-block centring records (3 x 16 B)
-    of the (block, projection) pairs it computes (texture blocks of
-    32 x 8 x 4 voxels, TMA bricks of 32 x 16 x 8)."""
+    of the n projections read once (the TMA path reads staged images of
+    8-byte elements, isx + 1 columns padded to an even count: float32 pairs,
+    isy rows; 16-bit column quads, isy + 1 rows), and for the FP32 form the
+    per-block centring records (3 x 16 B) of the (block, projection) pairs it
+    computes (texture blocks of 32 x 8 x 4 voxels, TMA bricks of 32 x 16 x
+    depth)."""
     px = 4 if form == "f32" else 2
     Lz = L if Lz is None else Lz
     if path == "tma":
-        align = 2 if form == "f32" else 4
-        pitch = -(-(isx + 1) // align) * align
-        total = 8 * L * L * Lz + n * pitch * isy * 2 * px
-        tile = (32, 16, 8)
+        pitch = -(-(isx + 1) // 2) * 2
+        rows = isy if form == "f32" else isy + 1
+        total = 8 * L * L * Lz + n * pitch * rows * 8
+        tile = (32, 16, depth)
     else:
         total = 8 * L * L * Lz + n * isx * isy * px
         tile = (32, 8, 4)
@@ -304,10 +308,10 @@ def whole_job_gups(updates_per_rank: int, steps: int, world: int, max_ms: float)
 def slab_of_rank(L: int, world: int, rank: int, granule: int = 8) -> tuple[int, int]:
     """(z0, nz) of this rank's slab when the z extent of an L^3 volume is
     split over world ranks, as the paper splits the z loop between threads
-    (Sect. 6): contiguous slabs of whole granules (the z depth of one TMA
-    brick, so no rank computes a partial brick except at the top of the
-    volume), in rank order, sizes differing by at most one granule.  A rank
-    left without a granule gets nz = 0."""
+    (Sect. 6): contiguous slabs of whole granules (8 slices, the depth of
+    the shallowest TMA brick, so no rank computes a partial brick except at
+    the top of the volume), in rank order, sizes differing by at most one
+    granule.  A rank left without a granule gets nz = 0."""
     if L < 1 or world < 1 or not 0 <= rank < world or granule < 1:
         raise ValueError("slab_of_rank: need L >= 1, world >= 1, 0 <= rank < world, granule >= 1")
     units = -(-L // granule)
@@ -785,8 +789,9 @@ def main():
     traffic = ncu_traffic(ksrc, f"{kname}_{head}_{args.L}.md") if args.n_proj == 496 and nz == args.L else None
     ncu_pct = ncu_fields(ksrc, f"{kname}_{head}_{args.L}x64.md", NCU_FRACTIONS)
     basis = ("shared-memory bandwidth" if head_path == "tma" else "the measured texture gather rate")
+    head_depth = depth_taken.get(head) or 16
     alg_bytes = algorithmic_bytes(vol.L, min(scan.n, 64), scan.isx, scan.isy, head, head_path,
-                                  k["computed_fraction"], nz)
+                                  k["computed_fraction"], nz, head_depth)
     avg_ms = k["kernel_ms"] / max(k["launches"], 1)
     hbm_peak, hbm_src = hbm_peak_gbs()
     bind = min((kk for kk in peak if kk != "min"), key=lambda kk: peak[kk])
@@ -806,7 +811,7 @@ def main():
         "gather_per_sm_clk_measured": {f: round(v, 3) for f, v in gather_rate.items()},
         "bounds_gups": {kk: round(v, 1) for kk, v in peak.items()},
         "diagnostics": {kk: round(v, 1) for kk, v in
-                        roofline_diagnostics_gups(head_path, head, sm_mhz, sms).items()},
+                        roofline_diagnostics_gups(head_path, head, sm_mhz, sms, head_depth).items()},
         "avg_launch_ms": round(k["kernel_ms"] / max(k["launches"], 1), 4),
         "launches": k["launches"],
         "traffic": traffic,

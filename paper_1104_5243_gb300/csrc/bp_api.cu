@@ -558,7 +558,11 @@ static double box_fit_fraction(const bp_ctx *c, const double *A, int m, int bz, 
 // path take the caller's choice; otherwise 16-deep bricks when their box
 // holds the sampled footprints of 98 % of the visible pairs (the rest take
 // the slower global-memory branch), else 8-deep bricks, and the texture path
-// when even the 8-deep box holds fewer than 90 % of them (coarse voxels).
+// when even the 8-deep box holds fewer than 40 % of them (coarse voxels).
+// The 40 % is measured: at 384^3 on the 1248x960 detector the 8-deep box
+// holds 60-75 % of the footprints and the TMA path still wins (f32 978
+// against 732 GUP/s, f16 1125 against 1105); at 256^3 it holds under 1 %
+// (468 against 593).
 // Measured on GB300 at 512^3 x 496 x 1248x960 (GUP/s per step for depths
 // 8 / 12 / 16): f32 1403 / 1379 / 1413, f16 1511 / 1497 / 1536; so 12 is
 // never the automatic choice.
@@ -572,7 +576,7 @@ static void choose_path(const bp_ctx *c, const double *A, int m, bool *tma, int 
         *zpl = 8;
         return;
     }
-    if (c->path == 0 && box_fit_fraction(c, A, m, 8, tma_rows(4, false)) < 0.9)
+    if (c->path == 0 && box_fit_fraction(c, A, m, 8, tma_rows(4, false)) < 0.4)
         *tma = false;
 }
 

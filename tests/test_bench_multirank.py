@@ -195,20 +195,25 @@ def test_hbm_peak_prefers_the_measured_file(tmp_path, monkeypatch):
 
 def test_algorithmic_bytes_of_a_launch():
     """Bytes one mid-step launch must move (the roofline's unit): the volume
-    read and written once, each projection's pair image once (f32 pairs of
-    8 B, pitch rounded to 2 pairs; 16-bit pairs of 4 B, pitch rounded to 4),
-    and for f32 the 48-byte centring record of every computed (brick,
-    projection) pair."""
+    read and written once, each projection's staged image once (8-byte
+    elements, 1250 columns: float32 pairs over 960 rows, 16-bit column quads
+    over 961), and for f32 the 48-byte centring record of every computed
+    (brick, projection) pair (bricks of 32 x 16 x depth)."""
     sys.path.insert(0, ROOT)
     import bench
     L, n, isx, isy = 512, 64, 1248, 960
-    bricks = 16 * 32 * 64
+    bricks16 = 16 * 32 * 32
     f32 = bench.algorithmic_bytes(L, n, isx, isy, "f32", "tma", 0.75)
-    assert f32 == 8 * L ** 3 + n * 1250 * isy * 8 + int(48 * n * bricks * 0.75)
+    assert f32 == 8 * L ** 3 + n * 1250 * isy * 8 + int(48 * n * bricks16 * 0.75)
+    f32_8 = bench.algorithmic_bytes(L, n, isx, isy, "f32", "tma", 0.75, depth=8)
+    assert f32_8 == 8 * L ** 3 + n * 1250 * isy * 8 + int(48 * n * 2 * bricks16 * 0.75)
     f16 = bench.algorithmic_bytes(L, n, isx, isy, "f16", "tma", 0.75)
-    assert f16 == 8 * L ** 3 + n * 1252 * isy * 4
+    assert f16 == 8 * L ** 3 + n * 1250 * (isy + 1) * 8
     # a z-slab of 64 slices: an eighth of the volume and of the bricks
     slab = bench.algorithmic_bytes(L, n, isx, isy, "f32", "tma", 0.75, Lz=64)
-    assert slab == 8 * L * L * 64 + n * 1250 * isy * 8 + int(48 * n * (bricks // 8) * 0.75)
+    assert slab == 8 * L * L * 64 + n * 1250 * isy * 8 + int(48 * n * (bricks16 // 8) * 0.75)
     tex = bench.algorithmic_bytes(L, n, isx, isy, "f32", "texture", 1.0)
     assert tex == 8 * L ** 3 + n * isx * isy * 4 + 48 * n * (16 * 64 * 128)
+    # the diagnostic shared-memory bytes per update: loads plus box fill
+    assert bench.tma_smem_bytes_per_update("f32", 16) == pytest.approx(16 + 120 * 58 * 8 / 8192)
+    assert bench.tma_smem_bytes_per_update("f16", 8) == pytest.approx(8 + 120 * 35 * 8 / 4096)

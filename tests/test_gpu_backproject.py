@@ -380,14 +380,15 @@ def test_tma_global_fallback_when_footprints_exceed_the_tile(depth):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("L,expect,depth", [(512, "tma", 16), (1024, "tma", 16), (256, "texture", None),
-                                            (128, "texture", None)])
+@pytest.mark.parametrize("L,expect,depth", [(512, "tma", 16), (1024, "tma", 16), (384, "tma", 8),
+                                            (256, "texture", None), (128, "texture", None)])
 def test_automatic_path_choice(dtype, L, expect, depth):
     """Automatic: the TMA path with the deepest brick whose box holds the
     footprints where voxels are fine (0.5 mm and 0.25 mm on the 1248x960
-    detector: 16-deep bricks), the texture path where they are coarse
-    (1 mm, 2 mm: a brick's footprint is wider than any staged box).  Eight
-    projections of the full scan; the result equals the forced choice."""
+    detector: 16-deep bricks; 0.67 mm: 8-deep bricks, most footprints fit),
+    the texture path where they are coarse (1 mm, 2 mm: a brick's footprint
+    is wider than any staged box).  Eight projections of the full scan; the
+    result equals the forced choice."""
     api = native()
     from paper_1104_5243_gb300 import _native as N
     scan = synth.SCANS["full"]
