@@ -646,7 +646,8 @@ def main():
         e2e = {"value": round(whole_job_gups(job_updates, args.steps, 1, wall * 1e3), 2), "unit": UNIT,
                "link": link,
                "step_ms": {"mean": round(wall * 1e3 / args.steps, 2), "median": round(statistics.median(walls), 2),
-                           "min": round(min(walls), 2), "max": round(max(walls), 2)},
+                           "min": round(min(walls), 2), "max": round(max(walls), 2),
+                           "each": [round(w, 2) for w in walls]},
                "device_resident_ms_per_step": forms.get("f32", {}).get("ms_per_step"),
                "h2d_bytes_per_step": int(stack_host.numel() * 4),
                "d2h_bytes_per_step": int(vol_host.numel() * 4),

@@ -53,6 +53,7 @@ struct bp_ctx {
     int nz_cap = 0;      // slab depth the volume was allocated for
     double R = 0, O[3] = {0, 0, 0};
     double O_cube[3] = {0, 0, 0};   // centre of voxel (0,0,0) of the L^3 grid
+    int z0 = 0;                     // the slab's first slice in the L^3 grid
     int isx = 0, isy = 0;
     bp_dtype dtype = BP_F32;
     int device = 0;
@@ -244,6 +245,7 @@ static bp_status create_context(bp_ctx **out, int L, int nz, int z0, double R, c
     c->R = R;
     for (int q = 0; q < 3; ++q)
         c->O_cube[q] = O[q];
+    c->z0 = z0;
     c->O[0] = O[0];
     c->O[1] = O[1];
     c->O[2] = O[2] + R * z0;   // centre of the slab's voxel (0,0,0)
@@ -313,6 +315,7 @@ extern "C" bp_status bp_move_slab(bp_ctx *c, int z0, int nz)
     CTX_CK(c, cudaStreamSynchronize(c->stream));
     CTX_CK(c, cudaStreamSynchronize(c->copy_stream));
     c->Lz = nz;
+    c->z0 = z0;
     c->O[2] = c->O_cube[2] + c->R * z0;
     return bp_reset(c);
 }
@@ -428,13 +431,15 @@ static inline float4 row4(const double *a, int r, double add_w)
                        (float)(a[4 * r + 2] + add_w * a[10]), (float)(a[4 * r + 3] + add_w * a[11]));
 }
 
-// Integer centring offsets (ku, kv): the pixel the centre of the volume
+// Integer centring offsets (ku, kv): the pixel the centre of the L^3 grid
 // projects to, rounded.  Over the volume |u - ku| then stays within the
-// volume's footprint half-width, far below |u|.
+// volume's footprint half-width, far below |u|.  A z-slab takes the whole
+// grid's offsets, so that its float32 rows (and the per-block centring
+// records built from them) equal the cube's.
 static inline void centre_offsets(const bp_ctx *c, const double *a, double *ku, double *kv)
 {
     const double h = 0.5 * (c->L - 1) * c->R;
-    const double X = c->O[0] + h, Y = c->O[1] + h, Z = c->O[2] + 0.5 * (c->Lz - 1) * c->R;
+    const double X = c->O_cube[0] + h, Y = c->O_cube[1] + h, Z = c->O_cube[2] + h;
     const double w = a[8] * X + a[9] * Y + a[10] * Z + a[11];
     const double u = (a[0] * X + a[1] * Y + a[2] * Z + a[3]) / w;
     const double v = (a[4] * X + a[5] * Y + a[6] * Z + a[7]) / w;
@@ -731,7 +736,7 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
                     c->centre_blocks[s] = nb;
                 }
                 centres = c->centres[s];
-                centre_batch(&cb, &rows[0][0][0], m, c->O, c->R);
+                centre_batch(&cb, &rows[0][0][0], m, c->O_cube, c->R);
             }
             int4 *boxes = nullptr;
             BoxSpec bs{};
@@ -749,7 +754,7 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
                 bs = BoxSpec{kTmaBU, tma_rows(zpl, quad), kTmaAlign, quad ? 1 : 0};
             }
             CTX_CK(c, launch_block_prepass(b, centres ? &cb : nullptr, g, c->isx, c->isy, tile[0], tile[1], tile[2],
-                                           masks, centres, boxes ? &bs : nullptr, boxes,
+                                           2 * c->z0, masks, centres, boxes ? &bs : nullptr, boxes,
                                            masks ? c->work_dev : nullptr, c->copy_stream));
         }
         CTX_CK(c, cudaEventRecord(c->copy_done[s], c->copy_stream));
@@ -1030,8 +1035,8 @@ extern "C" bp_status bp_adjoint(bp_ctx *c, const float *vol, int vol_on_device, 
         }
         if (blk) {
             CentreBatch cb;
-            centre_batch(&cb, &rows[0][0][0], m, c->O, c->R);
-            e = launch_block_prepass(fb, &cb, g, c->isx, c->isy, kAdjBlockX, kAdjBlockY, kAdjBlockZ, nullptr,
+            centre_batch(&cb, &rows[0][0][0], m, c->O_cube, c->R);
+            e = launch_block_prepass(fb, &cb, g, c->isx, c->isy, kAdjBlockX, kAdjBlockY, kAdjBlockZ, 2 * c->z0, nullptr,
                                      c->adj_centres, nullptr, nullptr, nullptr, c->stream);
             b.centres = c->adj_centres;
         }

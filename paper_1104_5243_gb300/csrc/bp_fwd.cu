@@ -387,7 +387,7 @@ __device__ int4 tma_box(const FwdBatch &b, int i, const VolGeom &g, int isx, int
 template <bool CENTRES>
 __global__ void __launch_bounds__(256)
 block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__ CentreBatch cb, const VolGeom g,
-                     int isx, int isy, int tx, int ty, int tz, int nbx, int nby, long long nblocks,
+                     int isx, int isy, int tx, int ty, int tz, int zoff2, int nbx, int nby, long long nblocks,
                      unsigned long long *__restrict__ masks, float4 *__restrict__ centres, const BoxSpec bs,
                      int4 *__restrict__ boxes, unsigned long long *__restrict__ work)
 {
@@ -403,7 +403,7 @@ block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__
                 m |= 1ull << i;
             int2 kb = make_int2((int)b.k[i].x, (int)b.k[i].y);
             if constexpr (CENTRES) {
-                const BlockRec rec = block_centre(b, cb, i, x0 + x1, y0 + y1, z0 + z1);
+                const BlockRec rec = block_centre(b, cb, i, x0 + x1, y0 + y1, z0 + z1 + zoff2);
                 centres[((size_t)0 * kMaxBatch + i) * nblocks + q] = rec.u;
                 centres[((size_t)1 * kMaxBatch + i) * nblocks + q] = rec.v;
                 centres[((size_t)2 * kMaxBatch + i) * nblocks + q] = rec.w;
@@ -424,7 +424,7 @@ block_prepass_kernel(const __grid_constant__ FwdBatch b, const __grid_constant__
 }
 
 cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const VolGeom &g, int isx, int isy,
-                                 int tx, int ty, int tz, unsigned long long *masks, float4 *centres,
+                                 int tx, int ty, int tz, int zoff2, unsigned long long *masks, float4 *centres,
                                  const BoxSpec *box, int4 *boxes, unsigned long long *work, cudaStream_t s)
 {
     if (b.n <= 0 || (!masks && !centres && !boxes))
@@ -436,12 +436,12 @@ cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const
     const long long nblocks = tile_count(g.L, g.Lz, tx, ty, tz);
     const unsigned grid = (unsigned)((nblocks + 255) / 256);
     if (centres && cb) {
-        block_prepass_kernel<true><<<grid, 256, 0, s>>>(b, *cb, g, isx, isy, tx, ty, tz, nbx, nby, nblocks, masks,
-                                                        centres, bs, boxes, work);
+        block_prepass_kernel<true><<<grid, 256, 0, s>>>(b, *cb, g, isx, isy, tx, ty, tz, zoff2, nbx, nby, nblocks,
+                                                        masks, centres, bs, boxes, work);
     } else {
         static const CentreBatch none = {};
-        block_prepass_kernel<false><<<grid, 256, 0, s>>>(b, none, g, isx, isy, tx, ty, tz, nbx, nby, nblocks, masks,
-                                                         nullptr, bs, boxes, work);
+        block_prepass_kernel<false><<<grid, 256, 0, s>>>(b, none, g, isx, isy, tx, ty, tz, zoff2, nbx, nby, nblocks,
+                                                         masks, nullptr, bs, boxes, work);
     }
     return cudaGetLastError();
 }

@@ -138,8 +138,11 @@ struct BoxSpec {
     int bu, bv, align;   // box columns and rows (elements), column alignment (elements)
     int quad;            // column quads: an element carries rows k and k + 1, stored at row k + 1
 };
+// zoff2: twice the global index of the volume's first slice (a z-slab of
+// the L^3 grid), so that the centring records of a slab's tiles are those
+// of the same tiles of the whole grid (cb built from the grid's origin).
 cudaError_t launch_block_prepass(const FwdBatch &b, const CentreBatch *cb, const VolGeom &g, int isx, int isy,
-                                 int tx, int ty, int tz, unsigned long long *masks, float4 *centres,
+                                 int tx, int ty, int tz, int zoff2, unsigned long long *masks, float4 *centres,
                                  const BoxSpec *box, int4 *boxes, unsigned long long *work, cudaStream_t s);
 
 // smem: accumulate each block's footprint in shared memory (kAdjTile pixels
