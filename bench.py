@@ -457,7 +457,7 @@ def time_volume(api, N, L: int, scan, stack, A, form: str, warmup: int, steps: i
     """GUP/s of the device-resident step at another volume size: nominal
     updates over the step time, and over the backprojection kernels' event
     time (nominal and computed updates), with the path and brick depth the
-    library chose."""
+    library chose (and, on the texture path, its warp layout)."""
     import torch
     from paper_1104_5243_gb300 import synth
     vol = synth.Volume(L)
@@ -491,6 +491,7 @@ def time_volume(api, N, L: int, scan, stack, A, form: str, warmup: int, steps: i
            "kernel_gups_computed": round(computed / (kms / steps / 1e3) / 1e9, 2),
            "computed_fraction": round(computed / nominal, 4), "path": bp.last_path,
            "brick_depth": bp.query(N.BP_QUERY_LAST_BRICK_DEPTH) if bp.last_path == "tma" else None,
+           "lanes_x": bp.query(N.BP_QUERY_LAST_LANES_X) if bp.last_path == "texture" else None,
            "steps": steps}
     bp.close()
     del out

@@ -70,12 +70,19 @@ typedef enum {
     /* 1: record a CUDA event pair around every backprojection kernel launch
      * on the context's stream, for bp_kernel_stats; 0 (default): off. */
     BP_OPT_TIMING = 3,
-    /* Warp layout of the backprojection kernel: 8, 16 or 32 lanes along x
+    /* Warp layout of the texture path's kernel: 8, 16 or 32 lanes along x
      * (the rest along z), or a two-digit code XY = X lanes along x by Y along
      * y (44, 42, 82, 24; the rest along z), or 108 (8 lanes along x, 8
-     * voxels per lane instead of 4).  Default 8 for BP_F32 projections and
-     * 108 for BP_F16 / BP_BF16 (fastest on GB300).  Changes speed only:
-     * every voxel still sums its projections in the same order. */
+     * voxels per lane instead of 4), or 0 (default): automatic, per batch --
+     * 24 where one voxel step spans 4 or more pixels at the volume centre
+     * (coarse voxels: 256^3 and coarser on a 1248x960 detector), else 8 for
+     * BP_F32 projections and 108 for BP_F16 / BP_BF16 (the fastest layouts
+     * measured on GB300 in each regime).  bp_query(BP_QUERY_LAST_LANES_X)
+     * reports the layout used.  Every voxel sums its projections in the same
+     * order whatever the layout; with per-projection centring the volumes
+     * are bit-identical, with per-block centring (the BP_F32 default) the
+     * blocks, and so the centring offsets, follow the layout and the float32
+     * rounding differs within the same accuracy. */
     BP_OPT_LANES_X = 4,
     /* Data path of the backprojection: 0 (default) automatic, 1 texture
      * gathers, 2 TMA-staged shared-memory tiles.  With per-projection
@@ -140,7 +147,8 @@ typedef enum {
     BP_QUERY_PROJECTIONS_ADDED = 2,  /* projections accumulated since create / reset / set_state */
     BP_QUERY_UPDATES_COMPUTED = 3,   /* voxel updates actually computed since create (culled blocks
                                       * excluded; synchronises the stream) */
-    BP_QUERY_LAST_BRICK_DEPTH = 4    /* brick depth of the last TMA-path batch (8, 12, 16; 0 none yet) */
+    BP_QUERY_LAST_BRICK_DEPTH = 4,   /* brick depth of the last TMA-path batch (8, 12, 16; 0 none yet) */
+    BP_QUERY_LAST_LANES_X = 5        /* warp layout of the last texture-path batch (BP_OPT_LANES_X codes; 0 none yet) */
 } bp_query_what;
 
 /* ---------------------------------------------------------------- context */

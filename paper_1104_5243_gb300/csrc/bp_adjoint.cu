@@ -32,10 +32,12 @@ __device__ __forceinline__ float recip_adj(float w)
 // of every voxel falls inside it without a test).  Then
 //   * footprint off the detector: the projection is skipped (all of its
 //     terms would be dropped -- block culling, as in the forward kernel);
-//   * footprint of at most kAdjTile pixels: the block zeroes a tile of that
-//     size, scatters its 4 weighted corners per update into it, and adds the
+//   * footprint of at most kAdjTile pixels: the block scatters its 4
+//     weighted corners per update into a tile of that size, and adds the
 //     tile's nonzero pixels on the detector to the image with one global
-//     atomic each (a few hundred per block instead of 4 per update);
+//     atomic each (a few hundred per block instead of 4 per update),
+//     zeroing each word it reads (the tile starts zeroed, so it is zero
+//     again for the next projection without a pass of its own);
 //   * larger footprint: global atomics per update, as in the direct kernel.
 // The tile accumulates in 32-bit fixed point with native integer
 // shared-memory atomics: float, and 64-bit integer, shared-memory atomics
@@ -68,8 +70,9 @@ constexpr int kAdjVPY = 4;
 // with offsets from the centre of its voxel box, so u and v stay within the
 // block's footprint.  The records centre u' = u - ku_b + 1; the kernel's
 // pixel offsets are ku_b - 1, kv_b - 1.
-// Four blocks per SM (measured: 533 GUP/s against 510 with the compiler's
-// own register choice, 500 with five blocks, 495 with six).
+// Four blocks per SM (measured: 538 GUP/s against 521 with three; with the
+// earlier four-barrier loop, 533 against 510 with the compiler's own
+// register choice, 500 with five blocks, 495 with six).
 template <bool IEEE, bool BLK>
 __global__ void __launch_bounds__(kThreads, 4)
 bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restrict__ vol, const VolGeom g,
@@ -79,8 +82,10 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
     static_assert(TX == kAdjBlockX && TY == kAdjBlockY && LZ == kAdjBlockZ, "pre-pass tile must be the block");
     __shared__ __align__(16) AdjAcc tile[kAdjTile];
     // (x0, y0, W, H); W = 0 culled, W < 0 too large.  Two slots: warp 0
-    // writes the next projection's plan while slower warps may still read
-    // this one (a culled projection has no barrier after the read).
+    // plans the next projection after its own scatter, while slower warps
+    // may still read this one; the barrier that ends the scatter publishes
+    // it.  A projection thus costs two block barriers (end of the scatter,
+    // end of the flush) and one when it is culled or untiled.
     __shared__ int4 plan[2];
     __shared__ float2 plan_scale[2];   // (scale, 1 / scale) of the fixed-point tile
     __shared__ float fsum_warp[kThreads / 32];
@@ -144,8 +149,9 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
     const float CY = fmaf(g.R, (float)((lane & 2) ? ye : by0), g.Oy);
     const float CZ = fmaf(g.R, (float)((lane & 4) ? ze : bz0), g.Oz);
 
-#pragma unroll 1
-    for (int i = 0; i < b.n; ++i) {
+    // warp 0: the footprint box and fixed-point scale of projection i into
+    // plan slot i & 1
+    auto plan_projection = [&](int i) {
         const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
         const int2 kc = b.k[i];
         if (threadIdx.x < 32) {
@@ -194,138 +200,149 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
                 plan[i & 1] = p;
             }
         }
-        __syncthreads();
+    };
+
+    // the tile starts zeroed; every flush leaves the part it used zeroed
+    for (int q = threadIdx.x; q < kAdjTile / 4; q += kThreads)
+        reinterpret_cast<int4 *>(tile)[q] = make_int4(0, 0, 0, 0);
+    plan_projection(0);
+    __syncthreads();
+#pragma unroll 1
+    for (int i = 0; i < b.n; ++i) {
+        const float4 ru = b.m[i][0], rv = b.m[i][1], rw = b.m[i][2];
+        const int2 kc = b.k[i];
         const int4 p = plan[i & 1];
         const float2 sc = plan_scale[i & 1];
-        if (p.z == 0)
-            continue;   // the block's footprint misses the detector
         float *img = out + b.out_off[i];
         const bool tiled = p.z > 0;
-        if (tiled) {
-            // kAdjTile is a multiple of 4: zero whole 16-byte words covering W * H
-            const int n16 = (p.z * p.w + 3) / 4;   // four int32 per 16-byte word
-            for (int q = threadIdx.x; q < n16; q += kThreads)
-                reinterpret_cast<int4 *>(tile)[q] = make_int4(0, 0, 0, 0);
-            __syncthreads();
-        }
-        // the voxels' rows and pixel offsets: the projection's (the plan
-        // above), or with BLK the block's recentred ones
-        float4 vu = ru, vv = rv, vw4 = rw;
-        int2 kb = kc;
-        if constexpr (BLK) {
-            vu = rec[0][i];
-            vv = rec[1][i];
-            vw4.w = rec[2][i].x;
-            kb = make_int2((int)rec[2][i].y - 1, (int)rec[2][i].z - 1);
-        }
-        if (tiled) {
-            // Every corner lands in the tile (the box covers the block's
-            // footprint with a pixel of margin), so there is no per-corner
-            // test; the clamp keeps the four addresses inside the array
-            // whatever the rounding.  The fixed-point scale (a power of two)
-            // is folded into the weight: the terms equal the scaled ones of
-            // the global path exactly.
-            const int W = p.z;
-            const unsigned qmax = (unsigned)(W * p.w - W - 2);
-            const int du = kb.x - p.x, dv = kb.y - p.y;
-            // the tile index of the top-left corner from the bits of the
-            // round-down sums (below): (bits(mv) - M) * W + bits(mu) - M +
-            // dv * W + du, in 32-bit unsigned arithmetic
-            const unsigned qoff = (unsigned)(dv * W + du) - kFloorMagicBits * (unsigned)(W + 1);
-#pragma unroll
-            for (int ky = 0; ky < kAdjVPY; ++ky) {
-                const float bu = fmaf(vu.y, Y[ky], fmaf(vu.z, Z, vu.w));
-                const float bv = fmaf(vv.y, Y[ky], fmaf(vv.z, Z, vv.w));
-                const float bw = fmaf(vw4.y, Y[ky], fmaf(vw4.z, Z, vw4.w));
-#pragma unroll
-                for (int k = 0; k < kVoxPerLane; ++k) {
-                    if (f[ky][k] == 0.f)
-                        continue;
-                    const float uw = fmaf(vu.x, X[k], bu);
-                    const float vw = fmaf(vv.x, X[k], bv);
-                    const float w = fmaf(vw4.x, X[k], bw);
-                    const float r = recip_adj<IEEE>(w);
-                    const float u = uw * r, v = vw * r;
-                    // floor without the conversion unit, which the
-                    // reciprocal and the four fixed-point conversions keep
-                    // busy (the floors and int conversions made it the
-                    // binding pipe: 9 of its operations per update): u +
-                    // 1.5 * 2^23 rounded down is floor(u) + 1.5 * 2^23
-                    // exactly for |u| < 2^22 (u stays within the block's
-                    // footprint), and its bits are the integer
-                    const float mu = __fadd_rd(u, kFloorMagic), mv = __fadd_rd(v, kFloorMagic);
-                    const float fu0 = mu - kFloorMagic, fv0 = mv - kFloorMagic;
-                    const unsigned q0 = min((unsigned)__float_as_int(mv) * (unsigned)W +
-                                                (unsigned)__float_as_int(mu) + qoff, qmax);
-                    const float fu = u - fu0, fv = v - fv0;
-                    const float s = f[ky][k] * ((r * sc.x) * r);
-                    const float sb = s * fv, st = s - sb;
-                    const float w_tr = st * fu, w_tl = st - w_tr;
-                    const float w_br = sb * fu, w_bl = sb - w_br;
-                    atomicAdd(&tile[q0], __float2int_rn(w_tl));
-                    atomicAdd(&tile[q0 + 1], __float2int_rn(w_tr));
-                    atomicAdd(&tile[q0 + W], __float2int_rn(w_bl));
-                    atomicAdd(&tile[q0 + W + 1], __float2int_rn(w_br));
-                }
+        if (p.z != 0) {
+            // the voxels' rows and pixel offsets: the projection's (the plan
+            // above), or with BLK the block's recentred ones
+            float4 vu = ru, vv = rv, vw4 = rw;
+            int2 kb = kc;
+            if constexpr (BLK) {
+                vu = rec[0][i];
+                vv = rec[1][i];
+                vw4.w = rec[2][i].x;
+                kb = make_int2((int)rec[2][i].y - 1, (int)rec[2][i].z - 1);
             }
-        } else {
-            // footprint larger than the tile: global atomics, pixels outside
-            // the detector dropped
-            const float ulo = (float)(-1 - kb.x), uhi = (float)(isx - kb.x);
-            const float vlo = (float)(-1 - kb.y), vhi = (float)(isy - kb.y);
-#pragma unroll
-            for (int ky = 0; ky < kAdjVPY; ++ky) {
-                const float bu = fmaf(vu.y, Y[ky], fmaf(vu.z, Z, vu.w));
-                const float bv = fmaf(vv.y, Y[ky], fmaf(vv.z, Z, vv.w));
-                const float bw = fmaf(vw4.y, Y[ky], fmaf(vw4.z, Z, vw4.w));
-#pragma unroll
-                for (int k = 0; k < kVoxPerLane; ++k) {
-                    if (f[ky][k] == 0.f)
-                        continue;
-                    const float uw = fmaf(vu.x, X[k], bu);
-                    const float vw = fmaf(vv.x, X[k], bv);
-                    const float w = fmaf(vw4.x, X[k], bw);
-                    const float r = recip_adj<IEEE>(w);
-                    const float u = uw * r, v = vw * r;
-                    if (!(u > ulo && u < uhi && v > vlo && v < vhi))
-                        continue;
-                    const float fu0 = floorf(u), fv0 = floorf(v);
-                    const int iu = (int)fu0 + kb.x, iv = (int)fv0 + kb.y;
-                    const float fu = u - fu0, fv = v - fv0;
-                    const float s = f[ky][k] * (r * r);
-                    const float sb = s * fv, st = s - sb;
-                    const float w_tr = st * fu, w_tl = st - w_tr;
-                    const float w_br = sb * fu, w_bl = sb - w_br;
-                    const bool in_l = iu >= 0, in_r = iu + 1 < isx, in_t = iv >= 0, in_b = iv + 1 < isy;
-                    const long long base = (long long)iv * isx + iu;
-                    if (in_t) {
-                        if (in_l) atomicAdd(img + base, w_tl);
-                        if (in_r) atomicAdd(img + base + 1, w_tr);
+            if (tiled) {
+                // Every corner lands in the tile (the box covers the block's
+                // footprint with a pixel of margin), so there is no per-corner
+                // test; the clamp keeps the four addresses inside the array
+                // whatever the rounding.  The fixed-point scale (a power of two)
+                // is folded into the weight: the terms equal the scaled ones of
+                // the global path exactly.
+                const int W = p.z;
+                const unsigned qmax = (unsigned)(W * p.w - W - 2);
+                const int du = kb.x - p.x, dv = kb.y - p.y;
+                // the tile index of the top-left corner from the bits of the
+                // round-down sums (below): (bits(mv) - M) * W + bits(mu) - M +
+                // dv * W + du, in 32-bit unsigned arithmetic
+                const unsigned qoff = (unsigned)(dv * W + du) - kFloorMagicBits * (unsigned)(W + 1);
+    #pragma unroll
+                for (int ky = 0; ky < kAdjVPY; ++ky) {
+                    const float bu = fmaf(vu.y, Y[ky], fmaf(vu.z, Z, vu.w));
+                    const float bv = fmaf(vv.y, Y[ky], fmaf(vv.z, Z, vv.w));
+                    const float bw = fmaf(vw4.y, Y[ky], fmaf(vw4.z, Z, vw4.w));
+    #pragma unroll
+                    for (int k = 0; k < kVoxPerLane; ++k) {
+                        if (f[ky][k] == 0.f)
+                            continue;
+                        const float uw = fmaf(vu.x, X[k], bu);
+                        const float vw = fmaf(vv.x, X[k], bv);
+                        const float w = fmaf(vw4.x, X[k], bw);
+                        const float r = recip_adj<IEEE>(w);
+                        const float u = uw * r, v = vw * r;
+                        // floor without the conversion unit, which the
+                        // reciprocal and the four fixed-point conversions keep
+                        // busy (the floors and int conversions made it the
+                        // binding pipe: 9 of its operations per update): u +
+                        // 1.5 * 2^23 rounded down is floor(u) + 1.5 * 2^23
+                        // exactly for |u| < 2^22 (u stays within the block's
+                        // footprint), and its bits are the integer
+                        const float mu = __fadd_rd(u, kFloorMagic), mv = __fadd_rd(v, kFloorMagic);
+                        const float fu0 = mu - kFloorMagic, fv0 = mv - kFloorMagic;
+                        const unsigned q0 = min((unsigned)__float_as_int(mv) * (unsigned)W +
+                                                    (unsigned)__float_as_int(mu) + qoff, qmax);
+                        const float fu = u - fu0, fv = v - fv0;
+                        const float s = f[ky][k] * ((r * sc.x) * r);
+                        const float sb = s * fv, st = s - sb;
+                        const float w_tr = st * fu, w_tl = st - w_tr;
+                        const float w_br = sb * fu, w_bl = sb - w_br;
+                        atomicAdd(&tile[q0], __float2int_rn(w_tl));
+                        atomicAdd(&tile[q0 + 1], __float2int_rn(w_tr));
+                        atomicAdd(&tile[q0 + W], __float2int_rn(w_bl));
+                        atomicAdd(&tile[q0 + W + 1], __float2int_rn(w_br));
                     }
-                    if (in_b) {
-                        if (in_l) atomicAdd(img + base + isx, w_bl);
-                        if (in_r) atomicAdd(img + base + isx + 1, w_br);
+                }
+            } else {
+                // footprint larger than the tile: global atomics, pixels outside
+                // the detector dropped
+                const float ulo = (float)(-1 - kb.x), uhi = (float)(isx - kb.x);
+                const float vlo = (float)(-1 - kb.y), vhi = (float)(isy - kb.y);
+    #pragma unroll
+                for (int ky = 0; ky < kAdjVPY; ++ky) {
+                    const float bu = fmaf(vu.y, Y[ky], fmaf(vu.z, Z, vu.w));
+                    const float bv = fmaf(vv.y, Y[ky], fmaf(vv.z, Z, vv.w));
+                    const float bw = fmaf(vw4.y, Y[ky], fmaf(vw4.z, Z, vw4.w));
+    #pragma unroll
+                    for (int k = 0; k < kVoxPerLane; ++k) {
+                        if (f[ky][k] == 0.f)
+                            continue;
+                        const float uw = fmaf(vu.x, X[k], bu);
+                        const float vw = fmaf(vv.x, X[k], bv);
+                        const float w = fmaf(vw4.x, X[k], bw);
+                        const float r = recip_adj<IEEE>(w);
+                        const float u = uw * r, v = vw * r;
+                        if (!(u > ulo && u < uhi && v > vlo && v < vhi))
+                            continue;
+                        const float fu0 = floorf(u), fv0 = floorf(v);
+                        const int iu = (int)fu0 + kb.x, iv = (int)fv0 + kb.y;
+                        const float fu = u - fu0, fv = v - fv0;
+                        const float s = f[ky][k] * (r * r);
+                        const float sb = s * fv, st = s - sb;
+                        const float w_tr = st * fu, w_tl = st - w_tr;
+                        const float w_br = sb * fu, w_bl = sb - w_br;
+                        const bool in_l = iu >= 0, in_r = iu + 1 < isx, in_t = iv >= 0, in_b = iv + 1 < isy;
+                        const long long base = (long long)iv * isx + iu;
+                        if (in_t) {
+                            if (in_l) atomicAdd(img + base, w_tl);
+                            if (in_r) atomicAdd(img + base + 1, w_tr);
+                        }
+                        if (in_b) {
+                            if (in_l) atomicAdd(img + base + isx, w_bl);
+                            if (in_r) atomicAdd(img + base + isx + 1, w_br);
+                        }
                     }
                 }
             }
         }
+        if (i + 1 < b.n)
+            plan_projection(i + 1);
+        __syncthreads();   // the scatter is done; the next plan is visible
         if (tiled) {
-            __syncthreads();
-            // one warp per tile row, lanes along the row (no index division);
-            // only the part of the tile on the detector
+            // one warp per tile row, lanes along the row; the pixels on the
+            // detector go to the image, and every word used is left zero
             const int c0 = max(0, -p.x), c1 = min(p.z, isx - p.x);
             const int r0 = max(0, -p.y), r1 = min(p.w, isy - p.y);
-            for (int row = r0 + (threadIdx.x >> 5); row < r1; row += kThreads / 32) {
+            for (int row = threadIdx.x >> 5; row < p.w; row += kThreads / 32) {
                 float *dst = img + (long long)(p.y + row) * isx + p.x;
-                const AdjAcc *src = tile + row * p.z;
-                for (int col = c0 + lane; col < c1; col += 32) {
+                AdjAcc *src = tile + row * p.z;
+                const bool on_row = row >= r0 && row < r1;
+                for (int col = lane; col < p.z; col += 32) {
                     const AdjAcc v = src[col];
-                    if (v != 0)
-                        atomicAdd(dst + col, (float)v * sc.y);
+                    if (v != 0) {
+                        src[col] = 0;
+                        if (on_row && col >= c0 && col < c1)
+                            atomicAdd(dst + col, (float)v * sc.y);
+                    }
                 }
             }
+            // the next projection scatters into the tile only if it is tiled
+            if (i + 1 < b.n && plan[(i + 1) & 1].z > 0)
+                __syncthreads();
         }
-        __syncthreads();   // tile and plan are reused by the next projection
     }
 }
 

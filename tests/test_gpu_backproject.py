@@ -405,8 +405,55 @@ def test_automatic_path_choice(dtype, L, expect, depth):
             assert bp.last_path == expect
             if expect == "tma":
                 assert bp.query(N.BP_QUERY_LAST_BRICK_DEPTH) == depth
+            else:
+                # coarse voxels (5 and 10 pixels per step): lanes along x and y
+                assert bp.query(N.BP_QUERY_LAST_LANES_X) == 24
             outs.append(bp.finalize().view(-1)[::97].cpu())
     assert torch.equal(outs[0], outs[1])
+
+
+LAYOUTS = (0, 8, 16, 32, 44, 42, 82, 24, 108)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", FP32_TOL), ("f16", FP16_TOL)])
+@pytest.mark.parametrize("case", ["tiny", "coarse"])
+def test_texture_layouts_match_oracle_and_each_other(case, dtype, tol):
+    """Every warp layout of the texture kernel, on the tiny scan (64^3 at
+    4 mm, 160x120 at 7.68 mm: 0.8 pixels per voxel step, where the automatic
+    layout is 8 for float32 and 108 for 16-bit projections) and on a coarse
+    case (96^3 at 2.67 mm, 24 projections of 624x480 at 0.616 mm: 6.6 pixels
+    per step, automatic layout 24), seeded random projections: each within
+    the tolerance of the FP64 oracle, and with per-projection centring
+    bit-identical to each other (every voxel sums the same float32 terms in
+    the same order whatever the layout)."""
+    api = native()
+    from paper_1104_5243_gb300 import _native as N
+    if case == "tiny":
+        scan, vol = synth.SCANS["tiny"], synth.Volume(64)
+        auto = 8 if dtype == "f32" else 108
+    else:
+        half = synth.SCANS["half"]
+        scan, vol = synth.Scan(n=24, isx=half.isx, isy=half.isy, pitch=half.pitch), synth.Volume(96)
+        auto = 24
+    A = oracle.carm_matrices(scan)
+    q = np.random.default_rng(11).random((scan.n, scan.isy, scan.isx), dtype=np.float32)
+    ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
+    qt = torch.from_numpy(q).cuda()
+    plain = []
+    for lanes in LAYOUTS:
+        for centre in ((1, 0) if dtype == "f32" else (None,)):
+            with api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype) as bp:
+                bp.set_option(N.BP_OPT_PATH, 1)
+                bp.set_option(N.BP_OPT_LANES_X, lanes)
+                if centre is not None:
+                    bp.set_option(N.BP_OPT_BLOCK_CENTRE, centre)
+                bp.add_projections(qt, A)
+                got = bp.finalize().cpu()
+                assert bp.query(N.BP_QUERY_LAST_LANES_X) == (lanes or auto)
+            assert rel_l2(got.numpy(), ref) <= tol, (lanes, centre)
+            if centre != 1:
+                plain.append(got)
+    assert all(torch.equal(plain[0], o) for o in plain[1:])
 
 
 def test_reciprocal_modes_accuracy_table():
