@@ -70,11 +70,11 @@ INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", 
 #   smem_atomics: four shared-memory atomics per update, conflict-free (one
 #     wavefront per warp instruction, one wavefront per SM per clock);
 #   mufu: one reciprocal per update.
-# Diagnostics: ncu's instructions per update and wavefronts per atomic
-# instruction (profiles/bp_adjoint_smem_kernel_256.md).
+# Diagnostics: ncu's instructions per nominal update and wavefronts per
+# atomic instruction (profiles/bp_adjoint_smem_kernel_256.md).
 ADJ_ATOMICS_PER_UPDATE = 4
-ADJ_INSTR_PER_UPDATE = 49.9
-ADJ_ATOMIC_WAVEFRONTS = 3.69
+ADJ_INSTR_PER_UPDATE = 53.1
+ADJ_ATOMIC_WAVEFRONTS = 3.67
 
 
 def adjoint_roofline_gups(sm_mhz: float, sms: int) -> dict:
