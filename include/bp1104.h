@@ -138,7 +138,22 @@ typedef enum {
      * centring offsets follow the brick, so the float32 rounding differs
      * between depths within the same accuracy.
      * bp_query(BP_QUERY_LAST_BRICK_DEPTH) reports the depth used. */
-    BP_OPT_BRICK_DEPTH = 9
+    BP_OPT_BRICK_DEPTH = 9,
+    /* BP_F16 storage: 1 scales each batch of projections by a power of four
+     * before rounding it to float16, 0 (default) stores the float32 values as
+     * they are.  Float16 overflows above 65504 and loses relative precision
+     * below 2^-14 (subnormals); ramp-filtered projections in physical units
+     * can fall outside that range.  With 1, a pass over each batch (on the
+     * copy stream) finds max|p| over its images; they are stored as
+     * p * 2^-2k with k chosen so that the largest value lies in
+     * [2^12, 2^14), and the kernels multiply the batch's sums by 2^2k (the
+     * scale folded into the weight 1/w^2 of every term; every step exact).
+     * Where the unscaled float16 values and their pair differences are
+     * normal numbers, the volume is bit-identical to the unscaled one;
+     * elsewhere the scaled form keeps float16's relative precision.  No
+     * effect for BP_F32 and BP_BF16 (bfloat16 has float32's exponent
+     * range). */
+    BP_OPT_PROJ_SCALE = 10
 } bp_option;
 
 /* Queries for bp_query. */

@@ -12,7 +12,7 @@ from . import build as _build
 BP_OK, BP_EINVAL, BP_ENOMEM, BP_ECUDA, BP_ESTATE, BP_ETIMEOUT = range(6)
 BP_F32, BP_F16, BP_BF16 = 0, 1, 2
 BP_OPT_IEEE_RCP, BP_OPT_BATCH, BP_OPT_TIMING, BP_OPT_LANES_X, BP_OPT_PATH, BP_OPT_CULL = 1, 2, 3, 4, 5, 6
-BP_OPT_HOST_DIRECT, BP_OPT_BLOCK_CENTRE, BP_OPT_BRICK_DEPTH = 7, 8, 9
+BP_OPT_HOST_DIRECT, BP_OPT_BLOCK_CENTRE, BP_OPT_BRICK_DEPTH, BP_OPT_PROJ_SCALE = 7, 8, 9, 10
 BP_QUERY_LAST_PATH, BP_QUERY_PROJECTIONS_ADDED, BP_QUERY_UPDATES_COMPUTED, BP_QUERY_LAST_BRICK_DEPTH = 1, 2, 3, 4
 BP_QUERY_LAST_LANES_X = 5
 STATUS_NAMES = {0: "BP_OK", 1: "BP_EINVAL", 2: "BP_ENOMEM", 3: "BP_ECUDA", 4: "BP_ESTATE", 5: "BP_ETIMEOUT"}

@@ -70,6 +70,8 @@ struct bp_ctx {
     cudaTextureObject_t tex[2][kMaxBatch] = {};
     cudaSurfaceObject_t surf[2][kMaxBatch] = {};
     float *staging[2] = {nullptr, nullptr};   // host-input staging for FP16/BF16
+    bool proj_scale = false;      // BP_OPT_PROJ_SCALE
+    unsigned *pmax[2] = {nullptr, nullptr};   // per input set: max|p| bits of the batch
     cudaEvent_t inputs_ready = nullptr;
     cudaEvent_t copy_done[2] = {nullptr, nullptr};
     cudaEvent_t kern_done[2] = {nullptr, nullptr};
@@ -162,6 +164,8 @@ static void release(bp_ctx *c)
     if (c->err_dev)
         cudaFree(c->err_dev);
     for (int s = 0; s < 2; ++s) {
+        if (c->pmax[s])
+            cudaFree(c->pmax[s]);
         if (c->masks[s])
             cudaFree(c->masks[s]);
         if (c->centres[s])
@@ -362,6 +366,11 @@ extern "C" bp_status bp_set_option(bp_ctx *c, int option, long long value)
         if (value != 0 && value != 1)
             return fail(c, BP_EINVAL, "bp_set_option: BLOCK_CENTRE takes 0 or 1");
         c->block_centre = value != 0;
+        return BP_OK;
+    case BP_OPT_PROJ_SCALE:
+        if (value != 0 && value != 1)
+            return fail(c, BP_EINVAL, "bp_set_option: PROJ_SCALE takes 0 or 1");
+        c->proj_scale = value != 0;
         return BP_OK;
     case BP_OPT_CULL:
         if (value != 0 && value != 1)
@@ -687,6 +696,12 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
         c->next_set ^= 1;
         CTX_CK(c, cudaStreamWaitEvent(c->copy_stream, c->kern_done[s], 0));
         const float *src0 = images + (size_t)c0 * img_elems;
+        // float16 storage with BP_OPT_PROJ_SCALE: a power-of-four scale per
+        // batch (proj_scale_k), from the images' maximum on the copy stream
+        const bool scaled = c->proj_scale && c->dtype == BP_F16;
+        if (scaled && c->pmax[s] == nullptr)
+            CTX_CK(c, cudaMalloc((void **)&c->pmax[s], sizeof(unsigned)));
+        const unsigned *pmax = scaled ? c->pmax[s] : nullptr;
         if (!tma && c->dtype == BP_F32 && !images_on_device && c->host_direct) {
             // host images straight into the arrays on the copy engine
             for (int j = 0; j < m; ++j)
@@ -701,9 +716,20 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
                                           cudaMemcpyHostToDevice, c->copy_stream));
                 src = c->staging[s];
             }
+            if (scaled) {
+                // max|p| over the batch's images, for its power-of-four scale
+                CTX_CK(c, cudaMemsetAsync(c->pmax[s], 0, sizeof(unsigned), c->copy_stream));
+                ConvBatch mb;
+                mb.n = m;
+                mb.pmax = nullptr;
+                for (int j = 0; j < m; ++j)
+                    mb.src[j] = src + (size_t)j * img_elems;
+                CTX_CK(c, launch_proj_absmax(mb, (long long)img_elems, c->pmax[s], c->copy_stream));
+            }
             if (tma) {
                 PairBatch pb;
                 pb.n = m;
+                pb.pmax = pmax;
                 for (int j = 0; j < m; ++j) {
                     pb.src[j] = src + (size_t)j * img_elems;
                     pb.dst[j] = static_cast<char *>(c->pairs[s]) + c->pair_slot_bytes * j;
@@ -712,6 +738,7 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
             } else {
                 ConvBatch cb;
                 cb.n = m;
+                cb.pmax = pmax;
                 for (int j = 0; j < m; ++j) {
                     cb.src[j] = src + (size_t)j * img_elems;
                     cb.surf[j] = c->surf[s][j];
@@ -728,6 +755,7 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
         // copy stream has waited for.  Tiles: the texture kernel's blocks or
         // the TMA path's bricks.
         FwdBatch b;
+        b.pmax = pmax;
         unsigned long long *masks = nullptr;
         float4 *centres = nullptr;
         int tile[3] = {kBrickX, kBrickY, 2 * zpl};
@@ -807,6 +835,7 @@ static bp_status add_projections(bp_ctx *c, const float *images, int images_on_d
         if (tma) {
             TmaBatch tb;   // 12 KB of kernel parameters
             tb.n = m;
+            tb.pmax = pmax;
             tb.isx = c->isx;
             tb.isy = c->isy;
             tb.pitch = (int)c->pair_pitch;
@@ -1057,6 +1086,7 @@ extern "C" bp_status bp_adjoint(bp_ctx *c, const float *vol, int vol_on_device, 
         b.blocks = nb;
         FwdBatch fb;   // the same rows in the forward convention, for the pre-pass
         fb.n = m;
+        fb.pmax = nullptr;
         double rows[kMaxBatch][3][4];
         for (int j = 0; j < m; ++j) {
             const double *a = A + 12 * (size_t)(c0 + j);

@@ -170,12 +170,15 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
         }
     }
 
+    // a batch stored with a power-of-four scale 2^(-2k) (b.pmax): the sums
+    // times 2^(2k), exactly; 1 otherwise
+    const float vs = b.pmax ? pow2f(2 * proj_scale_k(*b.pmax)) : 1.f;
     float *row = vol + ((size_t)z * L + y) * L;
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
         const int x = xb + LX * k;
         if (x < L)
-            row[x] = (accumulate ? row[x] : 0.f) + acc[k];
+            row[x] = (accumulate ? row[x] : 0.f) + acc[k] * vs;
     }
 }
 
@@ -512,7 +515,9 @@ convert_kernel(const __grid_constant__ ConvBatch b, int isx, int isy)
     const int i = blockIdx.z;
     if (j >= isx || i >= b.n)
         return;
-    const float f = b.src[i][(size_t)k * isx + j];
+    float f = b.src[i][(size_t)k * isx + j];
+    if (b.pmax)
+        f *= pow2f(-2 * proj_scale_k(*b.pmax));   // the batch's power-of-four scale (exact)
     if constexpr (MODE == 0) {
         surf2Dwrite<float>(f, b.surf[i], j * (int)sizeof(float), k);
     } else {
@@ -520,6 +525,59 @@ convert_kernel(const __grid_constant__ ConvBatch b, int isx, int isy)
                                               : __half_as_ushort(__float2half_rn(f));
         surf2Dwrite<unsigned short>(bits, b.surf[i], j * (int)sizeof(unsigned short), k);
     }
+}
+
+// max|p| over the batch's images as float bits (non-negative floats order
+// like their bits): a grid-stride pass per image (16-byte loads where every
+// image of the batch is 16-byte aligned and a multiple of 4 pixels), a warp
+// maximum, one atomic per warp.
+__device__ __forceinline__ unsigned abs_bits(float f)
+{
+    return __float_as_uint(f) & 0x7fffffffu;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+proj_absmax_kernel(const __grid_constant__ ConvBatch b, long long pixels, unsigned *pmax)
+{
+    const int i = blockIdx.y;
+    if (i >= b.n)
+        return;
+    const float *src = b.src[i];
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
+    unsigned m0 = 0u, m1 = 0u;
+    if constexpr (VEC) {
+        const float4 *src4 = reinterpret_cast<const float4 *>(src);
+        const long long n4 = pixels / 4;
+        for (long long j = t0; j < n4; j += step) {
+            const float4 v = src4[j];
+            m0 = max(m0, max(abs_bits(v.x), abs_bits(v.y)));
+            m1 = max(m1, max(abs_bits(v.z), abs_bits(v.w)));
+        }
+    } else {
+        for (long long j = t0; j < pixels; j += step)
+            m0 = max(m0, abs_bits(src[j]));
+    }
+    unsigned m = __reduce_max_sync(0xffffffffu, max(m0, m1));
+    if ((threadIdx.x & 31) == 0 && m != 0u)
+        atomicMax(pmax, m);
+}
+
+cudaError_t launch_proj_absmax(const ConvBatch &b, long long pixels, unsigned *pmax, cudaStream_t s)
+{
+    if (b.n <= 0 || pixels <= 0)
+        return cudaSuccess;
+    bool vec = pixels % 4 == 0;
+    for (int j = 0; j < b.n; ++j)
+        vec = vec && reinterpret_cast<uintptr_t>(b.src[j]) % 16 == 0;
+    const long long work = vec ? pixels / 4 : pixels;
+    const long long blocks = (work + 255) / 256;
+    dim3 grid((unsigned)(blocks < 64 ? blocks : 64), b.n);
+    if (vec)
+        proj_absmax_kernel<true><<<grid, 256, 0, s>>>(b, pixels, pmax);
+    else
+        proj_absmax_kernel<false><<<grid, 256, 0, s>>>(b, pixels, pmax);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_convert(const ConvBatch &b, int isx, int isy, int mode, cudaStream_t s)

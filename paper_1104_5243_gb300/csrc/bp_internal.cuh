@@ -33,8 +33,51 @@ struct FwdBatch {
     float4 m[kMaxBatch][3];
     float2 k[kMaxBatch];
     cudaTextureObject_t tex[kMaxBatch];
+    const unsigned *pmax;              // the batch's max|p| bits (proj_scale_k), NULL: no scale
     int n;
 };
+
+// Power-of-four scale of 16-bit storage (BP_OPT_PROJ_SCALE), one per batch.
+// From the bits of max|p| over the batch's projections (a non-negative
+// float, whose bits order like the values), the k for which
+// max|p| * 2^(-2k) lies in [2^12, 2^14): the staged values are p * 2^(-2k),
+// far from float16's overflow (65504, also for the pair differences, at
+// most twice the maximum) and from its subnormals (below 2^-14), and the
+// kernels multiply the batch's sums by 2^(2k).  Every term of a sum carries
+// the same factor 2^(-2k), so the scaled sums are the unscaled ones times
+// that power of two, exactly: the volume is bit-identical wherever the
+// unscaled staging is exact in its range.  k = 0 for an all-zero, infinite
+// or NaN batch; k is clamped to [-63, 63] (maxima below 2^-113 or above
+// 2^127 keep a smaller scaled maximum, or a larger one).
+__host__ __device__ inline int proj_scale_k(unsigned max_bits)
+{
+    if (max_bits == 0u || max_bits >= 0x7f800000u)
+        return 0;
+    const unsigned ex = max_bits >> 23, man = max_bits & 0x7fffffu;
+    int e;   // floor(log2(max|p|))
+    if (ex != 0) {
+        e = (int)ex - 127;
+    } else {
+        int hb = 22;
+        while (((man >> hb) & 1u) == 0u)
+            --hb;
+        e = hb - 149;
+    }
+    const int t = e - 13;
+    const int k = (t + (t & 1)) / 2;
+    return k < -63 ? -63 : k > 63 ? 63 : k;   // 2^(-2k) stays a normal float
+}
+
+// 2^q as a float for |q| <= 126.
+__host__ __device__ inline float pow2f(int q)
+{
+    union {
+        unsigned u;
+        float f;
+    } v;
+    v.u = (unsigned)(127 + q) << 23;
+    return v.f;
+}
 
 // Four values of the scalar type T: float4 for float, a plain aggregate for
 // double (the direct kernels are templates on T; the float64 instantiation
@@ -203,6 +246,7 @@ struct TmaBatch {
     const float4 *centres;             // per-brick centring records (NULL: per projection)
     const int4 *boxes;                 // per-(brick, projection) box decisions (pre-pass)
     long long bricks;                  // bricks of the volume (record plane stride)
+    const unsigned *pmax;              // the batch's max|p| bits (proj_scale_k), NULL: no scale
     float *final_out;                  // NULL, or a second destination of the updated volume
                                        // (device-addressable, same layout): the finished
                                        // volume written by the last batch's launch
@@ -217,6 +261,7 @@ cudaError_t launch_bp_tma(const TmaBatch &b, float *vol, const VolGeom &g, int p
 struct PairBatch {
     const float *src[kMaxBatch];
     void *dst[kMaxBatch];
+    const unsigned *pmax;              // the batch's max|p| bits (proj_scale_k), NULL: no scale
     int n;
 };
 // Images of the TMA path: rows() of them per projection (isy for pair
@@ -229,9 +274,13 @@ cudaError_t launch_pair_images(const PairBatch &b, int isx, int isy, int pitch, 
 struct ConvBatch {
     const float *src[kMaxBatch];
     cudaSurfaceObject_t surf[kMaxBatch];
+    const unsigned *pmax;              // the batch's max|p| bits (proj_scale_k), NULL: no scale
     int n;
 };
 cudaError_t launch_convert(const ConvBatch &b, int isx, int isy, int mode, cudaStream_t s);
+// max|p| over the batch's images (src, n; `pixels` each) as float bits into
+// *pmax, which the caller has zeroed.
+cudaError_t launch_proj_absmax(const ConvBatch &b, long long pixels, unsigned *pmax, cudaStream_t s);
 
 // Thread-local message for context-free entry points.
 void set_thread_error(const char *fmt, ...);

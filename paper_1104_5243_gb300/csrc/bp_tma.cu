@@ -467,11 +467,16 @@ bp_tma_kernel(const __grid_constant__ TmaBatch b, float *__restrict__ vol, const
     // then overlaps this launch instead of following it).
     float *sums = reinterpret_cast<float *>(dyn_smem);
     constexpr int P = St::kSumPitch;
+    // a batch staged with a power-of-four scale 2^(-2k) (b.pmax, 16-bit
+    // storage): the sums times 2^(2k), exactly
+    float vs = 1.f;
+    if constexpr (KIND != kPairF32)
+        vs = b.pmax ? pow2f(2 * proj_scale_k(*b.pmax)) : 1.f;
 #pragma unroll
     for (int q = 0; q < ZPL; ++q)
 #pragma unroll
         for (int kx = 0; kx < 4; ++kx)
-            sums[((zl0 + q) * kBrickY + yl) * P + tx + 8 * kx] = acc[q * 4 + kx];
+            sums[((zl0 + q) * kBrickY + yl) * P + tx + 8 * kx] = acc[q * 4 + kx] * vs;
     consumers_sync();
     float *const fin = b.final_out;
 #pragma unroll
@@ -602,8 +607,12 @@ pair_image_kernel(const __grid_constant__ PairBatch b, int isx, int isy, int pit
         dst[o] = make_uint2(__float_as_uint(l), __float_as_uint(__fsub_rn(r, l)));
     } else {
         const int k = j - 1;
-        const float tl = in ? pix(src, isx, isy, k, c - 1) : 0.f, tr = in ? pix(src, isx, isy, k, c) : 0.f;
-        const float bl = in ? pix(src, isx, isy, k + 1, c - 1) : 0.f, br = in ? pix(src, isx, isy, k + 1, c) : 0.f;
+        // the batch's power-of-four scale (exact; 1 without one)
+        const float sc = b.pmax ? pow2f(-2 * proj_scale_k(*b.pmax)) : 1.f;
+        const float tl = (in ? pix(src, isx, isy, k, c - 1) : 0.f) * sc;
+        const float tr = (in ? pix(src, isx, isy, k, c) : 0.f) * sc;
+        const float bl = (in ? pix(src, isx, isy, k + 1, c - 1) : 0.f) * sc;
+        const float br = (in ? pix(src, isx, isy, k + 1, c) : 0.f) * sc;
         const float dt = __fsub_rn(tr, tl), db = __fsub_rn(br, bl);
         unsigned lo, hi;
         if constexpr (KIND == kQuadF16) {

@@ -504,3 +504,64 @@ def test_detector_that_sees_part_of_the_volume_culls_and_matches_oracle():
     for path in (1, 2):
         got, _ = run_path(vol, scan, A, q, path)
         assert rel_l2(got.numpy(), ref) <= FP32_TOL
+
+
+def _scaled_run(vol, scan, A, q, dtype, path, scale, batch=None):
+    api = native()
+    from paper_1104_5243_gb300 import _native as N
+    with api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype) as bp:
+        bp.set_option(N.BP_OPT_PATH, path)
+        bp.set_option(N.BP_OPT_PROJ_SCALE, scale)
+        if batch is not None:
+            bp.set_option(N.BP_OPT_BATCH, batch)
+        bp.add_projections(torch.from_numpy(np.ascontiguousarray(q)).cuda(), A)
+        assert bp.last_path == ("texture" if path == 1 else "tma")
+        return bp.finalize().cpu()
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_projection_scale_is_exact_for_values_in_float16_range(path):
+    """The power-of-four scale of float16 storage (BP_OPT_PROJ_SCALE, one per
+    batch) changes the stored values and the batch's sums only by powers of
+    two: on integer-valued projections (0..1000, exact in float16 with and
+    without the scale, as are their pair differences) the volume is
+    bit-identical to the unscaled one, on both data paths, with batches of
+    8 projections whose maxima differ (the projections scaled by 2^-2 ..
+    2^3, still exact)."""
+    scan, vol = synth.SCANS["tiny"], synth.Volume(64)
+    A = oracle.carm_matrices(scan)
+    q = np.random.default_rng(21).integers(0, 1001, (scan.n, scan.isy, scan.isx)).astype(np.float32)
+    q *= (2.0 ** (np.arange(scan.n) % 6 - 2)).astype(np.float32)[:, None, None]   # 0.25 .. 8 per projection
+    off = _scaled_run(vol, scan, A, q, "f16", path, 0, batch=8)
+    on = _scaled_run(vol, scan, A, q, "f16", path, 1, batch=8)
+    assert torch.equal(off, on)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("magnitude", [1e6, 1e-7])
+def test_projection_scale_keeps_float16_accuracy_outside_its_range(path, magnitude):
+    """Projections of magnitude 1e6 overflow float16 (65504) and of 1e-7 fall
+    into its subnormals (below 6.1e-5; the smallest is 6e-8): stored as they
+    are, the volume is infinite or far off; with the power-of-four scale it
+    is within the float16 tolerance of the FP64 oracle, and both sides are
+    compared relative to the reference's own magnitude."""
+    scan, vol = synth.SCANS["tiny"], synth.Volume(64)
+    A = oracle.carm_matrices(scan)
+    q = (np.random.default_rng(22).random((scan.n, scan.isy, scan.isx)) * magnitude).astype(np.float32)
+    ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
+    on = _scaled_run(vol, scan, A, q, "f16", path, 1).numpy()
+    e_on = rel_l2(on, ref)
+    off = _scaled_run(vol, scan, A, q, "f16", path, 0).numpy()
+    e_off = rel_l2(off, ref) if np.all(np.isfinite(off)) else np.inf
+    print(f"magnitude {magnitude:g} path {path}: scaled {e_on:.2e}, unscaled {e_off:.2e}")
+    assert e_on <= FP16_TOL
+    assert e_off > 10 * FP16_TOL
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_projection_scale_applies_to_float16_only(dtype):
+    scan, vol = synth.SCANS["tiny"], synth.Volume(64)
+    A = oracle.carm_matrices(scan)
+    q = np.random.default_rng(23).random((scan.n, scan.isy, scan.isx), dtype=np.float32)
+    for path in (1, 2):
+        assert torch.equal(_scaled_run(vol, scan, A, q, dtype, path, 0), _scaled_run(vol, scan, A, q, dtype, path, 1))
