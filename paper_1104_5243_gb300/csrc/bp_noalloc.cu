@@ -151,12 +151,23 @@ static cudaError_t current_context_id(unsigned long long *id)
     });
     if (get_current == nullptr || get_id == nullptr)
         return cudaErrorNotSupported;
-    // make the device's primary context current if the thread has none yet
-    cudaError_t e = cudaFree(nullptr);
-    if (e != cudaSuccess)
-        return e;
     CUcontext ctx = nullptr;
-    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, id) != CUDA_SUCCESS)
+    if (get_current(&ctx) != CUDA_SUCCESS)
+        return cudaErrorDeviceUninitialized;
+    if (ctx == nullptr) {
+        // no context on this thread yet: cudaSetDevice initialises the
+        // current device's primary context and makes it current (a context
+        // the caller made current is left as it is); nothing is allocated
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaSetDevice(dev);
+        if (e != cudaSuccess)
+            return e;
+        if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr)
+            return cudaErrorDeviceUninitialized;
+    }
+    if (get_id(ctx, id) != CUDA_SUCCESS)
         return cudaErrorDeviceUninitialized;
     return cudaSuccess;
 }
