@@ -565,3 +565,34 @@ def test_projection_scale_applies_to_float16_only(dtype):
     q = np.random.default_rng(23).random((scan.n, scan.isy, scan.isx), dtype=np.float32)
     for path in (1, 2):
         assert torch.equal(_scaled_run(vol, scan, A, q, dtype, path, 0), _scaled_run(vol, scan, A, q, dtype, path, 1))
+
+
+def test_projection_scale_with_host_inputs_and_the_fused_call():
+    """The scaled float16 path through the other input routes: host images
+    (staged on the copy stream, their maximum taken there) and the fused
+    add_projections_finalize into pinned host memory give the same volume,
+    bit for bit, as device images with separate calls; ragged batches."""
+    api = native()
+    from paper_1104_5243_gb300 import _native as N
+    scan, vol = synth.SCANS["tiny"], synth.Volume(64)
+    A = oracle.carm_matrices(scan)
+    q = (np.random.default_rng(24).random((scan.n, scan.isy, scan.isx)) * 3e5).astype(np.float32)
+    outs = []
+    for route in ("device", "host", "fused"):
+        with api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype="f16") as bp:
+            bp.set_option(N.BP_OPT_PROJ_SCALE, 1)
+            bp.set_option(N.BP_OPT_BATCH, 10)
+            qt = torch.from_numpy(q)
+            if route == "device":
+                bp.add_projections(qt.cuda(), A)
+                outs.append(bp.finalize().cpu())
+            elif route == "host":
+                bp.add_projections(qt.pin_memory(), A)
+                outs.append(bp.finalize().cpu())
+            else:
+                host = torch.empty(bp.shape, dtype=torch.float32).pin_memory()
+                bp.add_projections_finalize(qt.cuda(), A, host)
+                outs.append(host.clone())
+    ref = oracle.backproject(vol.L, vol.R, vol.O, q, A)
+    assert np.all(np.isfinite(outs[0].numpy())) and rel_l2(outs[0].numpy(), ref) <= FP16_TOL
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
