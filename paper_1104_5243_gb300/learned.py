@@ -92,22 +92,49 @@ class LearnedRowFilter(torch.nn.Module):
     parameter then moves one frequency band, which keeps the optimisation
     well conditioned: in the tap basis the low-frequency (DC) direction,
     to which the reconstruction error is by far most sensitive, dominates
-    every tap's gradient."""
+    every tap's gradient.
 
-    def __init__(self, T: int = 64, tau: float = 1.0):
+    response="cosine" (default) learns the T/2 + 1 coefficients directly;
+    response="mlp" makes them the output of a small multilayer perceptron of
+    the normalised frequency k / (T/2) (1 -> hidden -> hidden -> 1, tanh),
+    a smooth response with fewer degrees of freedom per band.  Its last layer
+    starts at zero, so either form starts from the plain ramp."""
+
+    def __init__(self, T: int = 64, tau: float = 1.0, response: str = "cosine", hidden: int = 16):
         super().__init__()
+        if response not in ("cosine", "mlp"):
+            raise ValueError(f"response must be 'cosine' or 'mlp', got {response!r}")
         self.tau = float(tau)
+        self.response = response
         central = torch.from_numpy(ramlak_taps(T, tau))
         m = torch.arange(T, dtype=torch.float64) - T // 2
         k = torch.arange(T // 2 + 1, dtype=torch.float64)
         basis = torch.cos(2.0 * math.pi * m[:, None] * k[None, :] / T).float()
-        self.coef = torch.nn.Parameter(torch.zeros(T // 2 + 1))
         self.register_buffer("ramlak_central", central)
         self.register_buffer("basis", basis)
+        if response == "cosine":
+            self.coef = torch.nn.Parameter(torch.zeros(T // 2 + 1))
+        else:
+            self.register_buffer("freq", (k / (T // 2)).float()[:, None])
+            self.mlp = torch.nn.Sequential(torch.nn.Linear(1, hidden), torch.nn.Tanh(),
+                                           torch.nn.Linear(hidden, hidden), torch.nn.Tanh(),
+                                           torch.nn.Linear(hidden, 1))
+            torch.nn.init.zeros_(self.mlp[-1].weight)
+            torch.nn.init.zeros_(self.mlp[-1].bias)
+            # output scale 1 / hidden: an Adam step of the last layer (hidden
+            # weights) then moves a coefficient about as far as one step of
+            # the cosine form, so both train at the same learning rate
+            self.out_scale = 1.0 / hidden
+
+    def coefficients(self) -> torch.Tensor:
+        """The T/2 + 1 cosine coefficients of the learned change."""
+        if self.response == "cosine":
+            return self.coef
+        return self.mlp(self.freq).squeeze(-1) * self.out_scale
 
     @property
     def delta(self) -> torch.Tensor:
-        return self.basis @ self.coef
+        return self.basis @ self.coefficients()
 
     def delta_at_pitch(self, factor: int) -> torch.Tensor:
         """The learned change resampled to a detector `factor` times finer:
@@ -115,10 +142,11 @@ class LearnedRowFilter(torch.nn.Module):
         1 / factor (the row filter approximates a convolution integral, so
         taps scale with the pixel pitch); factor * T taps."""
         T = self.basis.shape[0]
-        m = (torch.arange(T * factor, dtype=torch.float64, device=self.coef.device) - T * factor // 2) / factor
-        k = torch.arange(T // 2 + 1, dtype=torch.float64, device=self.coef.device)
+        dev = self.basis.device
+        m = (torch.arange(T * factor, dtype=torch.float64, device=dev) - T * factor // 2) / factor
+        k = torch.arange(T // 2 + 1, dtype=torch.float64, device=dev)
         basis = torch.cos(2.0 * math.pi * m[:, None] * k[None, :] / T)
-        return (basis @ self.coef.double() / factor).float()
+        return (basis @ self.coefficients().detach().double() / factor).float()
 
     @property
     def taps(self) -> torch.Tensor:
@@ -171,14 +199,15 @@ def ramp_fdk(pre: torch.Tensor, scan, bp: api.Backprojector, A) -> torch.Tensor:
 
 
 def train(steps: int = 200, batch: int = 8, T: int = 64, lr: float = 1e-4, seed0: int = 1000,
-          wl: Workload | None = None, log=None):
+          wl: Workload | None = None, log=None, response: str = "cosine"):
     """Train the taps through the GPU forward and backward kernels on batches
-    of seeded phantoms (seeds seed0 + k).  Returns (module, losses)."""
+    of seeded phantoms (seeds seed0 + k); response selects the filter's
+    parameterisation (LearnedRowFilter).  Returns (module, losses)."""
     wl = wl or Workload()
     scan, vol = wl.scan, wl.volume
     A = api.carm_matrices(scan)
     data = PhantomData(wl, A)
-    filt = LearnedRowFilter(T, tau=api.iso_pitch(scan)).cuda()
+    filt = LearnedRowFilter(T, tau=api.iso_pitch(scan), response=response).cuda()
     opt = torch.optim.Adam(filt.parameters(), lr=lr)
     bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy)
     pool = [data.sample(seed0 + k) for k in range(batch * 4)]

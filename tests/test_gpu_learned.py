@@ -142,3 +142,19 @@ def test_learned_filter_beats_ramp_fdk_on_heldout_phantoms():
     # over to the 4x finer detector (measured 0.3-0.7 %).  What is required
     # there: the resampled filter costs nothing against the ramp FDK.
     assert full["mse_learned"] <= 1.002 * full["mse_ramp"]
+
+
+def test_mlp_response_form_trains_through_the_kernels():
+    """The small-MLP response form of the learned filter (its cosine
+    coefficients the output of a 1-16-16-1 tanh network of the frequency):
+    200 Adam steps through the forward and backward kernels lower the
+    training loss and beat the plain ramp FDK on every held-out seed
+    (measured: 3 % lower MSE, the cosine form 9 %)."""
+    lm = learned()
+    torch.manual_seed(0)
+    filt, losses = lm.train(steps=200, batch=8, response="mlp", lr=3e-4)
+    assert losses[-1] < losses[0]
+    res = lm.evaluate(filt, [9000 + k for k in range(4)])
+    print(f"MLP form: held-out MSE learned {res['mse_learned']:.4e} ramp {res['mse_ramp']:.4e}")
+    assert res["mse_learned"] < 0.99 * res["mse_ramp"]
+    assert all(a < b for a, b in zip(res["per_seed_learned"], res["per_seed_ramp"]))
