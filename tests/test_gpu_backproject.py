@@ -169,18 +169,25 @@ def test_gpu_matrices_match_oracle():
 
 @pytest.mark.parametrize("L,dtype,tol", [(512, "f32", FP32_TOL), (512, "f16", FP16_TOL), (512, "bf16", BF16_TOL),
                                          (1024, "f32", FP32_TOL), (1024, "f16", FP16_TOL),
-                                         (1024, "bf16", BF16_TOL)])
+                                         (1024, "bf16", BF16_TOL), (256, "f32", FP32_TOL),
+                                         (256, "f16", FP16_TOL), (256, "bf16", BF16_TOL)])
 def test_full_size_sampled_voxels(L, dtype, tol):
-    """512^3 and 1024^3 x 496 x 1248x960, uniform timing stack, in the launch
-    configuration the benchmark times (batches of 64, device input, the
-    automatic path: TMA for every storage type); the oracle evaluates 4096
-    sampled voxels one by one."""
+    """256^3, 512^3 and 1024^3 x 496 x 1248x960, uniform timing stack, in the
+    launch configuration the benchmark times (batches of 64, device input,
+    the automatic path: TMA at 512^3 and 1024^3, the texture path with lanes
+    along x and y at 256^3, for every storage type); the oracle evaluates
+    4096 sampled voxels one by one."""
     api = native()
     scan, vol = synth.SCANS["full"], synth.Volume(L)
     A = oracle.carm_matrices(scan)
     stack = synth.uniform_stack(scan.n, scan.isy, scan.isx)
     bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=dtype)
     bp.add_projections(torch.from_numpy(stack).cuda(), A)
+    from paper_1104_5243_gb300 import _native as N
+    if L == 256:
+        assert bp.last_path == "texture" and bp.query(N.BP_QUERY_LAST_LANES_X) == 24
+    else:
+        assert bp.last_path == "tma" and bp.query(N.BP_QUERY_LAST_BRICK_DEPTH) == 16
     got = bp.finalize().view(-1)
     rng = np.random.default_rng(7)
     idx = rng.integers(0, L ** 3, size=4096)
