@@ -118,7 +118,7 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
             f[ky][k] = (live && x < L) ? vol[((size_t)z * L + y) * L + x] : 0.f;
         }
     }
-    const float Z = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)z, g.Oz);
+    const float Z = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)(z + g.z0), g.Oz);
     if constexpr (BLK) {
         if (threadIdx.x < 3 * kMaxBatch) {
             const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -147,7 +147,7 @@ bp_adjoint_smem_kernel(const __grid_constant__ AdjBatch b, const float *__restri
     // corner of the block's voxel box taken by lane c < 8 of warp 0
     const float CX = fmaf(g.R, (float)((lane & 1) ? xe : bx0), g.Ox);
     const float CY = fmaf(g.R, (float)((lane & 2) ? ye : by0), g.Oy);
-    const float CZ = fmaf(g.R, (float)((lane & 4) ? ze : bz0), g.Oz);
+    const float CZ = fmaf(g.R, (float)(((lane & 4) ? ze : bz0) + g.z0), g.Oz);
 
     // warp 0: the footprint box and fixed-point scale of projection i into
     // plan slot i & 1

@@ -462,7 +462,8 @@ static VolGeom vol_geom(const bp_ctx *c)
     g.R = (float)c->R;
     g.Ox = (float)c->O[0];
     g.Oy = (float)c->O[1];
-    g.Oz = (float)c->O[2];
+    g.Oz = (float)c->O_cube[2];
+    g.z0 = c->z0;
     return g;
 }
 

@@ -65,7 +65,7 @@ direct_adjoint_kernel(const __grid_constant__ AdjBatchT<T> b, const T *__restric
         X[k] = fma(g.R, (T)x, g.Ox);
     }
     const T Y = fma(g.R, (T)y, g.Oy);
-    const T Z = fma(g.R, (T)z, g.Oz);
+    const T Z = fma(g.R, (T)(z + g.z0), g.Oz);
 
 #pragma unroll 1
     for (int i = 0; i < b.n; ++i) {
@@ -135,7 +135,7 @@ direct_backproject_kernel(const __grid_constant__ DirectBatchT<T> b, const T *__
     const int L = g.L;
     if (x >= L)
         return;
-    const T X = fma(g.R, (T)x, g.Ox), Y = fma(g.R, (T)y, g.Oy), Z = fma(g.R, (T)z, g.Oz);
+    const T X = fma(g.R, (T)x, g.Ox), Y = fma(g.R, (T)y, g.Oy), Z = fma(g.R, (T)(z + g.z0), g.Oz);
     T acc = T(0);
 #pragma unroll 1
     for (int i = 0; i < b.n; ++i) {

@@ -119,7 +119,7 @@ bp_fwd_kernel(const __grid_constant__ FwdBatch b, float *__restrict__ vol, const
     for (int k = 0; k < VPL; ++k)
         X[k] = BLK ? g.R * ((float)(xb + LX * k) - hx) : fmaf(g.R, (float)(xb + LX * k), g.Ox);
     const float Y = BLK ? g.R * ((float)y - hy) : fmaf(g.R, (float)y, g.Oy);
-    const float Z = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)z, g.Oz);
+    const float Z = BLK ? g.R * ((float)z - hz) : fmaf(g.R, (float)(z + g.z0), g.Oz);
 
     float acc[VPL];
 #pragma unroll
@@ -274,7 +274,7 @@ __device__ bool footprint_hits(const FwdBatch &b, int i, const VolGeom &g, int i
     for (int c = 0; c < 8; ++c) {
         const float X = fmaf(g.R, (float)((c & 1) ? x1 : x0), g.Ox);
         const float Y = fmaf(g.R, (float)((c & 2) ? y1 : y0), g.Oy);
-        const float Z = fmaf(g.R, (float)((c & 4) ? z1 : z0), g.Oz);
+        const float Z = fmaf(g.R, (float)(((c & 4) ? z1 : z0) + g.z0), g.Oz);
         const float w = fmaf(rw.x, X, fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w)));
         const float r = 1.0f / w;
         const float u = fmaf(ru.x, X, fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w))) * r;
@@ -349,7 +349,7 @@ __device__ int4 tma_box(const FwdBatch &b, int i, const VolGeom &g, int isx, int
     for (int c = 0; c < 8; ++c) {
         const float X = fmaf(g.R, (float)((c & 1) ? x1 : x0), g.Ox);
         const float Y = fmaf(g.R, (float)((c & 2) ? y1 : y0), g.Oy);
-        const float Z = fmaf(g.R, (float)((c & 4) ? z1 : z0), g.Oz);
+        const float Z = fmaf(g.R, (float)(((c & 4) ? z1 : z0) + g.z0), g.Oz);
         const float w = fmaf(rw.x, X, fmaf(rw.y, Y, fmaf(rw.z, Z, rw.w)));
         const float r = 1.0f / w;
         const float u = fmaf(ru.x, X, fmaf(ru.y, Y, fmaf(ru.z, Z, ru.w))) * r;

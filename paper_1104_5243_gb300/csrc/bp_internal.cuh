@@ -112,6 +112,10 @@ template <typename T>
 struct VolGeomT {
     int L, Lz;
     T R, Ox, Oy, Oz;
+    // first slice of a z-slab in the L^3 grid (0 for the whole cube); Oz is
+    // the cube's origin, so a slice's z coordinate R (z + z0) + Oz is formed
+    // identically by a slab context and by one holding the whole cube
+    int z0;
 };
 using VolGeom = VolGeomT<float>;
 
@@ -202,10 +206,12 @@ cudaError_t launch_bp_adjoint(const AdjBatch &b, const float *vol, const VolGeom
 //   * float32 "pair images": element c of row k holds (p[k][c-1],
 //     p[k][c] - p[k][c-1]); an update reads two elements (rows iv, iv+1);
 //   * 16-bit "column quads": element c of stored row j (image row k = j - 1)
-//     holds the 16-bit pairs (p[k][c-1], p[k+1][c-1]) and (p[k][c] -
-//     p[k][c-1], p[k+1][c] - p[k+1][c-1]), the differences taken in float32
-//     and rounded once; an update reads one element and interpolates both
-//     rows along u with one packed two-lane FMA.
+//     holds the pixel cell's bilinear coefficients as 16-bit pairs
+//     (tl, bl - tl) and (tr - tl, (br - bl) - (tr - tl)) (tl = p[k][c-1],
+//     tr = p[k][c], bl = p[k+1][c-1], br = p[k+1][c]), the differences taken
+//     in float32 and rounded once; an update reads one element, forms both
+//     coefficient pairs along u with one packed two-lane FMA and the
+//     interpolant with one mixed-precision FMA.
 // ZPL (voxels per lane along z) sets the brick depth: 4, 6 or 8 (8-, 12-
 // and 16-deep bricks).  Deeper bricks spread the per-projection work of a
 // thread over more updates but need taller boxes; the host picks, per

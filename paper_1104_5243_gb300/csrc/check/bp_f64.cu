@@ -55,6 +55,7 @@ bp::VolGeomT<double> geom(int L, double R, const double *O)
     g.Ox = O[0];
     g.Oy = O[1];
     g.Oz = O[2];
+    g.z0 = 0;
     return g;
 }
 

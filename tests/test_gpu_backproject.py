@@ -321,12 +321,13 @@ def test_tma_path_against_texture_path(dtype):
     if dtype == "f32":
         assert torch.equal(tex, tma)
     else:
-        # both within the storage bar; the TMA path's two-lane FMA rounds
-        # the row values once more to the storage type, which about doubles
-        # the storage error on this ramp-filtered phantom (measured 1.6e-4
-        # against 8.3e-5 for f16, 1.2e-3 against 6.4e-4 for bf16)
+        # both within the storage bar; the TMA path's coefficient quads
+        # round the fractions fu, fv and the two coefficient sums to the
+        # storage type once more, about 2.6x the storage error on this
+        # ramp-filtered phantom (measured 2.1e-4 against 8.3e-5 for f16,
+        # 1.66e-3 against 6.4e-4 for bf16)
         assert e_tma <= tol and e_tex <= tol
-        assert e_tma <= 2.5 * e_tex
+        assert e_tma <= 3.0 * e_tex
     # the defaults (per-block centring for float32) match the oracle too
     for path, fixed in ((1, tex), (2, tma)):
         blk, _ = run_path(vol, scan, A, q, path, dtype)
