@@ -62,7 +62,7 @@ TEXELS_PER_UPDATE = 4
 # profiles/<kernel>_<form>_512x64.md), and shared-memory bandwidth including
 # the TMA fill of each brick's box.
 ISSUE_PER_SM_CLK = 128.0
-INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 24.4, ("tma", "f16"): 24.3}
+INSTR_PER_UPDATE = {("texture", "f32"): 29.8, ("texture", "f16"): 26.0, ("tma", "f32"): 24.4, ("tma", "f16"): 23.3}
 # Adjoint (B^T, the same arithmetic per update as B, with the four corner
 # terms scattered instead of gathered):
 #   fp32_pipe: the forward's 20.5 FP32-pipe operations (geometry, floor,
