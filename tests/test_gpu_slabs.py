@@ -23,7 +23,8 @@ def case(L=37):
 @pytest.mark.parametrize("dtype,path", [("f32", 0), ("f32", 1), ("f16", 0), ("bf16", 1)])
 def test_slab_by_slab_reconstruction_matches_the_oracle(dtype, path):
     """37^3 in slabs of 10 slices (10, 10, 10, 7), host output, against the
-    oracle and against one context holding the whole cube."""
+    oracle and against one context holding the whole cube (bit for bit for
+    the 16-bit forms)."""
     api = native()
     from paper_1104_5243_gb300 import _native as N
     scan, vol, A, q = case()
@@ -47,7 +48,14 @@ def test_slab_by_slab_reconstruction_matches_the_oracle(dtype, path):
     print(f"{dtype} path {path}: slabs against the oracle {rel_l2(got, ref):.3e}, against the whole cube "
           f"{rel_l2(got, whole):.3e}")
     assert rel_l2(got, ref) <= tol
-    assert rel_l2(got, whole) <= (1e-6 if dtype == "f32" else 1e-5)
+    if dtype == "f32":
+        # per-block centring: slabs whose bricks cut the cube's differently
+        # agree to float32 rounding
+        assert rel_l2(got, whole) <= 1e-6
+    else:
+        # per-projection centring and z coordinates from the global slice
+        # index: every slab computes the cube's values bit for bit
+        assert np.array_equal(got, whole)
 
 
 def test_slab_adjoint_equals_the_adjoint_of_the_zero_padded_volume():
