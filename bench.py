@@ -20,6 +20,8 @@ weak scaling, no collective); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import contextlib
+import gc
 import json
 import os
 import statistics
@@ -211,6 +213,21 @@ def ncu_traffic(kernel_file: str, profile: str):
 # issue rate, each in % of its peak, from the committed full ncu capture of
 # the dominant kernel on the 512^3 x 64 case.
 NCU_FRACTIONS = ["fma_pipe_pct", "smem_wavefronts_pct", "dram_pct", "issue_active_pct"]
+
+
+@contextlib.contextmanager
+def gc_paused():
+    """Python's cyclic garbage collector off inside a timed region (collected
+    just before), as timeit does: a collection of the bench's heap inside a
+    step stalls the host thread that issues the copies and launches."""
+    gc.collect()
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
 
 
 # ---------------------------------------------------------------------------
@@ -577,6 +594,47 @@ def main():
     depth_taken = {}
     clocks = None
     rcp_modes = None
+    # End to end through the public API: pinned host projections in, the
+    # finished volume out to pinned host memory, every step, in the one call
+    # that does both (the last launch stores the volume into the host buffer).
+    # Measured before the device-resident forms: after the clock sampler's
+    # nvidia-smi had run and been stopped, steps of this region took up to
+    # 54-99 ms against 45 ms with unchanged kernel times (host copies held up).
+    e2e = None
+    if not args.no_e2e:
+        vol_host = torch.empty((nz, args.L, args.L), dtype=torch.float32).pin_memory()
+        bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype="f32", nz=nz, z0=z0)
+
+        def step_e2e():
+            bp.reset()
+            bp.add_projections_finalize(stack_host, A, vol_host)
+
+        for _ in range(max(args.warmup, 5)):   # host-copy warm-up: the first pinned transfers run slower
+            step_e2e()
+        barrier()
+        with gc_paused():
+            t0 = time.perf_counter()
+            walls = []
+            for _ in range(args.steps):
+                ts = time.perf_counter()
+                step_e2e()     # returns after the finished volume is in host memory
+                walls.append((time.perf_counter() - ts) * 1e3)
+            torch.cuda.synchronize()
+            t_end = time.perf_counter()
+        wall = rank_max(t_end - t0)
+        bp.close()
+        link = link_rates(stack_host, stack, vol_host, out, stream)
+        e2e = {"value": round(whole_job_gups(job_updates, args.steps, 1, wall * 1e3), 2), "unit": UNIT,
+               "link": link,
+               "step_ms": {"mean": round(wall * 1e3 / args.steps, 2), "median": round(statistics.median(walls), 2),
+                           "min": round(min(walls), 2), "max": round(max(walls), 2),
+                           "each": [round(w, 2) for w in walls]},
+               "device_resident_ms_per_step": None,   # filled in after the forms below
+               "h2d_bytes_per_step": int(stack_host.numel() * 4),
+               "d2h_bytes_per_step": int(vol_host.numel() * 4),
+               "step": "reset + bp_add_projections_finalize (pinned host images in, finished volume into "
+                       "pinned host memory)"}
+
     for form in args.forms.split(","):
         bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype=form, nz=nz, z0=z0)
         bp.set_option(N.BP_OPT_PATH, {"auto": 0, "texture": 1, "tma": 2}[args.path])
@@ -592,7 +650,7 @@ def main():
         bp.kernel_stats()
         computed0 = bp.query(N.BP_QUERY_UPDATES_COMPUTED)
         barrier()
-        with ClockSampler(smi_id) as cs:
+        with ClockSampler(smi_id) as cs, gc_paused():
             t0 = torch.cuda.Event(enable_timing=True)
             t1 = torch.cuda.Event(enable_timing=True)
             t0.record(stream)
@@ -619,41 +677,8 @@ def main():
                                              updates * args.steps / (ms / 1e3) / 1e9)
         bp.close()
 
-    # End to end through the public API: pinned host projections in, the
-    # finished volume out to pinned host memory, every step, in the one call
-    # that does both (the last launch stores the volume into the host buffer).
-    e2e = None
-    if not args.no_e2e:
-        vol_host = torch.empty((nz, args.L, args.L), dtype=torch.float32).pin_memory()
-        bp = api.Backprojector(vol.L, vol.R, vol.O, scan.isx, scan.isy, dtype="f32", nz=nz, z0=z0)
-
-        def step_e2e():
-            bp.reset()
-            bp.add_projections_finalize(stack_host, A, vol_host)
-
-        for _ in range(args.warmup):
-            step_e2e()
-        barrier()
-        t0 = time.perf_counter()
-        walls = []
-        for _ in range(args.steps):
-            ts = time.perf_counter()
-            step_e2e()     # returns after the finished volume is in host memory
-            walls.append((time.perf_counter() - ts) * 1e3)
-        torch.cuda.synchronize()
-        wall = rank_max(time.perf_counter() - t0)
-        bp.close()
-        link = link_rates(stack_host, stack, vol_host, out, stream)
-        e2e = {"value": round(whole_job_gups(job_updates, args.steps, 1, wall * 1e3), 2), "unit": UNIT,
-               "link": link,
-               "step_ms": {"mean": round(wall * 1e3 / args.steps, 2), "median": round(statistics.median(walls), 2),
-                           "min": round(min(walls), 2), "max": round(max(walls), 2),
-                           "each": [round(w, 2) for w in walls]},
-               "device_resident_ms_per_step": forms.get("f32", {}).get("ms_per_step"),
-               "h2d_bytes_per_step": int(stack_host.numel() * 4),
-               "d2h_bytes_per_step": int(vol_host.numel() * 4),
-               "step": "reset + bp_add_projections_finalize (pinned host images in, finished volume into "
-                       "pinned host memory)"}
+    if e2e is not None:
+        e2e["device_resident_ms_per_step"] = forms.get("f32", {}).get("ms_per_step")
 
     # The other volume sizes of the full-scale and precision workloads
     # (256^3: 1 mm voxels, and 1024^3: 0.25 mm, from the same 496
